@@ -1,0 +1,124 @@
+/*
+ * cq.h -- C ABI of the GB300 direct-SCF Fock-build library (libcq.so).
+ *
+ * What it computes (ChronusQ paper, Sec. "Reference Wave Functions",
+ * Eq. 2c_fock, and Sec. "General Infrastructure for the Unified Treatment of
+ * Electronic Spin", Eq. pauli_sep): Coulomb and exchange matrices over
+ * contracted Cartesian Gaussian basis functions,
+ *     J_{mn} = sum_{ls} (mn|ls) P_{ls},     K_{mn} = sum_{ls} (ml|sn) P_{ls},
+ * evaluated directly (integrals recomputed on every call, "direct SCF"),
+ * with Schwarz x density screening, for real symmetric, complex Hermitian
+ * and two-component (Pauli scalar + 3 spin components) densities; and the
+ * drivers built on it (RHF/GHF SCF, RT-TDHF steps).
+ *
+ * Conventions for every entry point:
+ *   - Matrices are row-major nbf x nbf.  Complex matrices are interleaved
+ *     (re, im) doubles (the layout of complex128).
+ *   - Basis functions are Cartesian, lexicographic within a shell
+ *     (s; x,y,z; xx,xy,xz,yy,yz,zz); every Cartesian component of every
+ *     contracted function is normalised to unit self-overlap.
+ *   - "device" pointers are CUDA device memory owned by the caller; "host"
+ *     pointers are host memory owned by the caller.  The library never frees
+ *     caller memory.  Scratch memory the library needs is allocated inside the
+ *     basis handle (cq_basis_create / first use) and freed by cq_basis_destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work of
+ *     a call is enqueued on that stream; calls that return host values
+ *     synchronise it.
+ *   - No entry point aborts or traps.  Every failure returns a negative
+ *     cq_status and sets a thread-local message read by cq_last_error().
+ */
+#ifndef CQ_H
+#define CQ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CQ_OK = 0,
+    CQ_ERR_INVALID_ARG = -1,
+    CQ_ERR_CUDA = -2,
+    CQ_ERR_OOM = -3,
+    CQ_ERR_NOT_CONVERGED = -4,
+    CQ_ERR_NUMERIC = -5,
+    CQ_ERR_TIMEOUT = -6,
+    CQ_ERR_UNSUPPORTED = -7
+} cq_status;
+
+/* Density kinds for cq_fock_build (Eq. spin_generalization). */
+typedef enum {
+    CQ_DENS_REAL_SYM = 0,      /* P real symmetric (one spin block, RHF)     */
+    CQ_DENS_COMPLEX_HERM = 1,  /* P complex Hermitian (RT-TDHF, one block)   */
+    CQ_DENS_PAULI4 = 2         /* P^0..P^3 complex Hermitian (GHF, 2C)       */
+} cq_dens_kind;
+
+typedef enum { CQ_PREC_FP64 = 0, CQ_PREC_MIXED = 1 } cq_prec;
+
+typedef struct cq_basis cq_basis;   /* opaque; owns device copies + scratch */
+
+/* cq_basis_create: build a basis from host arrays (copied; caller keeps
+ * ownership).  Contracted Cartesian Gaussian shells (paper Sec.
+ * "Input Specification": CGTO expansions, segmented contraction).
+ *   natom, xyz[3*natom] (bohr), Z[natom]            nuclei
+ *   nshell, shell_atom[nshell], shell_L[nshell] (0..2),
+ *   shell_nprim[nshell] (1..16)
+ *   exps[sum nprim] (>0), coefs[sum nprim]          raw contraction
+ *                                                   coefficients of
+ *                                                   unnormalised primitives
+ * Errors: CQ_ERR_INVALID_ARG (L>2, nprim out of range, exponent <= 0, NULL),
+ * CQ_ERR_CUDA / CQ_ERR_OOM on device failures.  Runs on the current device
+ * and synchronises it.  The Schwarz table (cq_schwarz) is computed here. */
+int cq_basis_create(int natom, const double* xyz, const int* Z, int nshell,
+                    const int* shell_atom, const int* shell_L,
+                    const int* shell_nprim, const double* exps,
+                    const double* coefs, cq_basis** out);
+
+/* Number of basis functions, shells, shell pairs. */
+int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npair);
+
+void cq_basis_destroy(cq_basis* b);
+
+/* cq_schwarz: Schwarz factors Q_ab = sqrt(max_{m in a, n in b} |(mn|mn)|)
+ * (screening of the direct build, Sec. "Reference Wave Functions": LinK-like
+ * screening).  Q: device, nshell*nshell doubles (row-major, symmetric), or
+ * NULL to only (re)compute the internal table.  Enqueued on `stream`. */
+int cq_schwarz(cq_basis* b, double* Q, void* stream);
+
+typedef struct {
+    double schwarz_tol;  /* skip a shell quartet when Q_ab Q_cd max|P| < tol (1e-14) */
+    double mixed_tol;    /* CQ_PREC_MIXED: quartets with bound < mixed_tol in FP32 */
+    int prec;            /* cq_prec */
+    int want_J, want_K;  /* 0/1 */
+} cq_fock_opts;
+
+typedef struct {
+    unsigned long long quartets_fp64;  /* contracted shell quartets evaluated in FP64 */
+    unsigned long long quartets_fp32;  /* ... in FP32 (mixed precision)             */
+    unsigned long long prim_fp64, prim_fp32; /* primitive quartets                   */
+    double ms;                          /* device time of the build (CUDA events)   */
+} cq_fock_stats;
+
+/* cq_fock_build: J and K of a density (Eq. 2c_fock; Pauli components per
+ * Eq. pauli_sep).  All pointers device, row-major:
+ *   REAL_SYM:      P nbf^2 f64 (symmetric); J nbf^2 f64; K nbf^2 f64.
+ *   COMPLEX_HERM:  P nbf^2 c128 (Hermitian); J nbf^2 f64 (J of Re P; J of the
+ *                  antisymmetric Im P vanishes); K nbf^2 c128 (Hermitian).
+ *   PAULI4:        P 4*nbf^2 c128 (P^0..P^3, each Hermitian); J nbf^2 f64 =
+ *                  J[P^0]; K 4*nbf^2 c128 = K[P^0..P^3].
+ * J or K may be NULL when opts->want_J / want_K is 0.  opts NULL = defaults
+ * (schwarz_tol 1e-14, FP64, J and K).  stats may be NULL; when given, the
+ * call synchronises `stream` to fill it.  Hermiticity of P is assumed, not
+ * checked: only the symmetric part of Re P and the antisymmetric part of
+ * Im P contribute. */
+int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
+                  const cq_fock_opts* opts, cq_fock_stats* stats, void* stream);
+
+/* Nuclear repulsion energy of the basis' nuclei (host result). */
+int cq_nuclear_repulsion(const cq_basis* b, double* E);
+
+const char* cq_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CQ_H */

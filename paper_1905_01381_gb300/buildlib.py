@@ -1,0 +1,142 @@
+"""Build libcq.so for sm_103a: generate the per-class ERI code, compile every
+translation unit with nvcc in parallel and link the shared library in-tree
+(paper_1905_01381_gb300/_build/libcq.so)."""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+BUILD = os.path.join(HERE, "_build")
+GEN = os.path.join(BUILD, "gen")
+OBJ = os.path.join(BUILD, "obj")
+SO = os.path.join(BUILD, "libcq.so")
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                  "--expt-relaxed-constexpr", "-Xptxas=-warn-spills", "-I", CSRC, "-I", GEN,
+                  "-I", os.path.join(os.path.dirname(HERE), "include")]
+HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu"]
+LIBS = ["-lcublas", "-lcusolver"]
+
+PCS = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+
+
+def qclasses():
+    out = []
+    for i, X in enumerate(PCS):
+        for Y in PCS[:i + 1]:
+            out.append((X, Y))
+    return out
+
+
+def gen_sources():
+    sys.path.insert(0, CSRC)
+    import gen_eri  # noqa: E402
+    sys.path.pop(0)
+    stats = gen_eri.main(GEN)
+    tus = []
+    for qc, (X, Y) in enumerate(qclasses()):
+        la, lb, lc, ld = X[0], X[1], Y[0], Y[1]
+        cls = f"{la}{lb}{lc}{ld}"
+        src = [f"// generated by build.py: class ({cls})",
+               '#include "cq_common.cuh"',
+               "namespace cq {",
+               f'#include "eri_{cls}.cuh"',
+               "}",
+               '#include "cq_jk.cuh"',
+               "namespace cq {",
+               f"void launch_jk_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
+               "{",
+               "    const int blocks = (a.ntasks * 32 + JK_THREADS - 1) / JK_THREADS;",
+               "    if (blocks == 0) return;",
+               f"    if (fp32) jk_kernel<{la}, {lb}, {lc}, {ld}, float><<<blocks, JK_THREADS, 0, s>>>(a);",
+               f"    else jk_kernel<{la}, {lb}, {lc}, {ld}, double><<<blocks, JK_THREADS, 0, s>>>(a);",
+               "}"]
+        if X == Y:
+            src += [f"void launch_schwarz_{la}{lb}(const JKArgs& a, int begin, int end, float* Qf, double* Qd, cudaStream_t s)",
+                    "{",
+                    "    const int n = end - begin;",
+                    "    if (n <= 0) return;",
+                    f"    schwarz_kernel<{la}, {lb}><<<(n + 63) / 64, 64, 0, s>>>(a, begin, end, Qf, Qd);",
+                    "}"]
+        src.append("}  // namespace cq")
+        path = os.path.join(GEN, f"cls_{cls}.cu")
+        text = "\n".join(src) + "\n"
+        if not os.path.exists(path) or open(path).read() != text:
+            with open(path, "w") as fh:
+                fh.write(text)
+        tus.append(path)
+    # dispatch table
+    d = ['#include "cq_internal.h"', "namespace cq {"]
+    for (X, Y) in qclasses():
+        d.append(f"void launch_jk_{X[0]}{X[1]}{Y[0]}{Y[1]}(const JKArgs&, int, cudaStream_t);")
+    for X in PCS:
+        d.append(f"void launch_schwarz_{X[0]}{X[1]}(const JKArgs&, int, int, float*, double*, cudaStream_t);")
+    d.append("const LaunchJK JK_LAUNCH[NQC] = {" +
+             ", ".join(f"launch_jk_{X[0]}{X[1]}{Y[0]}{Y[1]}" for X, Y in qclasses()) + "};")
+    d.append("const LaunchSchwarz SCHWARZ_LAUNCH[NPC] = {" +
+             ", ".join(f"launch_schwarz_{X[0]}{X[1]}" for X in PCS) + "};")
+    d.append("}  // namespace cq")
+    path = os.path.join(GEN, "cq_dispatch.cu")
+    text = "\n".join(d) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        with open(path, "w") as fh:
+            fh.write(text)
+    tus.append(path)
+    return tus, stats
+
+
+def _deps_mtime():
+    m = 0.0
+    for f in os.listdir(CSRC):
+        if f.endswith((".cuh", ".h", ".py")):
+            m = max(m, os.path.getmtime(os.path.join(CSRC, f)))
+    m = max(m, os.path.getmtime(os.path.join(os.path.dirname(HERE), "include", "cq.h")))
+    return m
+
+
+def _compile(src, verbose=False):
+    obj = os.path.join(OBJ, os.path.basename(src).replace(".cu", ".o"))
+    dm = max(_deps_mtime(), os.path.getmtime(src))
+    if os.path.exists(obj) and os.path.getmtime(obj) >= dm:
+        return obj, ""
+    cmd = ["nvcc", "-c", src, "-o", obj + ".tmp"] + NVFLAGS
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    os.replace(obj + ".tmp", obj)
+    return obj, r.stderr
+
+
+def build(jobs: int | None = None, verbose: bool = False) -> str:
+    os.makedirs(GEN, exist_ok=True)
+    os.makedirs(OBJ, exist_ok=True)
+    tus, _ = gen_sources()
+    srcs = [os.path.join(CSRC, s) for s in HAND_SOURCES] + tus
+    # heaviest TUs first so the parallel build finishes early
+    srcs.sort(key=lambda s: -os.path.getsize(s) if "cls_" not in s else
+              -os.path.getsize(os.path.join(GEN, "eri_" + os.path.basename(s)[4:8] + ".cuh")))
+    jobs = jobs or max(1, os.cpu_count() or 1)
+    with cf.ThreadPoolExecutor(jobs) as ex:
+        res = list(ex.map(lambda s: _compile(s, verbose), srcs))
+    objs = [r[0] for r in res]
+    if verbose:
+        for o, err in res:
+            if err.strip():
+                print(os.path.basename(o), err.strip()[:2000])
+    newest = max(os.path.getmtime(o) for o in objs)
+    if not os.path.exists(SO) or os.path.getmtime(SO) < newest:
+        tmp = SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["nvcc", "-shared", "-o", tmp] + ARCH + objs + LIBS)
+        os.replace(tmp, SO)
+    return SO
+
+
+if __name__ == "__main__":
+    import time
+    t = time.time()
+    print(build(verbose="-v" in sys.argv), f"{time.time() - t:.1f}s")

@@ -1,0 +1,393 @@
+// Basis set-up: shell normalisation, primitive-pair preparation, the Boys
+// table and the Schwarz factors (direct-SCF integral screening).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+
+#include "cq_internal.h"
+#include "cq_jk.cuh"
+
+namespace cq {
+
+const int PC_L[NPC][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char* what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? CQ_ERR_OOM : CQ_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- kernels
+
+// Boys table: row k holds F_m(T_k), T_k = k/16, m = 0..15 (FP64) and
+// m = 0..12 (FP32), plus e^{-T_k}.  F_15 from the power series
+//   F_m(T) = e^{-T} sum_i (2T)^i / ((2m+1)(2m+3)...(2m+2i+1)),
+// lower orders by downward recursion.
+__global__ void boys_table_kernel(double* tab, float* tabf)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= BOYS_NT) return;
+    const double T = k * 0.0625;
+    const int mtop = 15;
+    double term = 1.0 / (2 * mtop + 1), sum = term;
+    for (int i = 1; i < 1000; ++i) {
+        term *= 2.0 * T / (2 * mtop + 2 * i + 1);
+        sum += term;
+        if (term < 1e-19 * sum) break;
+    }
+    const double e = exp(-T);
+    double F[16];
+    F[mtop] = e * sum;
+    for (int m = mtop - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + e) / (2 * m + 1);
+    for (int m = 0; m < 16; ++m) tab[k * BOYS_D_COLS + m] = F[m];
+    tab[k * BOYS_D_COLS + BOYS_D_EXP] = e;
+    tab[k * BOYS_D_COLS + BOYS_D_EXP + 1] = 0.0;
+    for (int m = 0; m < BOYS_F_EXP; ++m) tabf[k * BOYS_F_COLS + m] = (float)F[m];
+    tabf[k * BOYS_F_COLS + BOYS_F_EXP] = (float)e;
+}
+
+__device__ double dfact_odd(int n)  // (n)!! for odd n >= -1
+{
+    double r = 1.0;
+    for (int k = n; k > 1; k -= 2) r *= k;
+    return r;
+}
+
+// Contraction coefficients c_k N_L(alpha_k) / sqrt(S), N_L = (2a/pi)^{3/4}(4a)^{L/2},
+// S the self-overlap of the x^L component (closed form of a same-centre
+// Gaussian product: prod_x (2l-1)!!/(2p)^l * (pi/p)^{3/2}).
+__global__ void normalize_kernel(int nsh, const int* L, const int* np, const int* poff,
+                                 const double* ex, const double* co, double* out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsh) return;
+    const int l = L[s], n = np[s], o = poff[s];
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < n; ++k) {
+        const double a = ex[o + k];
+        out[o + k] = co[o + k] * pow(2.0 * a / pi, 0.75) * pow(4.0 * a, 0.5 * l);
+    }
+    double S = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double p = ex[o + i] + ex[o + j];
+            S += out[o + i] * out[o + j] * dfact_odd(2 * l - 1) / pow(2.0 * p, (double)l) *
+                 pow(pi / p, 1.5);
+        }
+    const double f = 1.0 / sqrt(S);
+    for (int k = 0; k < n; ++k) out[o + k] *= f;
+}
+
+// Per-function factor of a Cartesian component relative to the x^L one:
+// sqrt((2L-1)!! / ((2lx-1)!!(2ly-1)!!(2lz-1)!!)).
+__global__ void scale_kernel(int nsh, const int* L, const int* bfo, double* scale)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsh) return;
+    const int l = L[s];
+    int c = 0;
+    for (int lx = l; lx >= 0; --lx)
+        for (int ly = l - lx; ly >= 0; --ly, ++c) {
+            const int lz = l - lx - ly;
+            scale[bfo[s] + c] =
+                sqrt(dfact_odd(2 * l - 1) / (dfact_odd(2 * lx - 1) * dfact_odd(2 * ly - 1) * dfact_odd(2 * lz - 1)));
+        }
+}
+
+// Primitive-pair data, one thread per shell pair.
+__global__ void pair_prep_kernel(int npair, const PairHdr* pairs, const double* ctr, const int* np,
+                                 const int* poff, const double* ex, const double* coef, PrimPair* out,
+                                 PrimPairF* outf)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npair) return;
+    const PairHdr h = pairs[p];
+    const double* A = ctr + 3 * h.a;
+    const double* B = ctr + 3 * h.b;
+    const double AB2 = h.AB[0] * h.AB[0] + h.AB[1] * h.AB[1] + h.AB[2] * h.AB[2];
+    const double kfac = 1.4142135623730951 * pow(3.14159265358979323846, 1.25);  // sqrt(2) pi^{5/4}
+    int q = h.poff;
+    for (int i = 0; i < np[h.a]; ++i)
+        for (int j = 0; j < np[h.b]; ++j, ++q) {
+            const double a = ex[poff[h.a] + i], b = ex[poff[h.b] + j];
+            const double z = a + b;
+            PrimPair o;
+            o.zeta = z;
+            o.oo2z = 0.5 / z;
+            for (int x = 0; x < 3; ++x) {
+                o.P[x] = (a * A[x] + b * B[x]) / z;
+                o.PA[x] = o.P[x] - A[x];
+            }
+            o.K = coef[poff[h.a] + i] * coef[poff[h.b] + j] * exp(-a * b / z * AB2) * kfac / z;
+            out[q] = o;
+            PrimPairF f;
+            f.zeta = (float)o.zeta; f.oo2z = (float)o.oo2z; f.K = (float)o.K;
+            for (int x = 0; x < 3; ++x) { f.P[x] = (float)o.P[x]; f.PA[x] = (float)o.PA[x]; }
+            outf[q] = f;
+        }
+}
+
+}  // namespace cq
+
+using namespace cq;
+
+extern "C" const char* cq_last_error(void) { return cq::g_err.c_str(); }
+
+static void free_basis(cq_basis* b)
+{
+    if (!b) return;
+    void* ptrs[] = {b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
+                    b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
+                    b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,
+                    b->d_Kp, b->d_Dmax, b->d_cnt};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (b->ev0) cudaEventDestroy(b->ev0);
+    if (b->ev1) cudaEventDestroy(b->ev1);
+    delete b;
+}
+
+template <typename T>
+static int upload(T** d, const std::vector<T>& h)
+{
+    int rc = dalloc(d, h.size());
+    if (rc) return rc;
+    if (!h.empty()) CQ_CUDA(cudaMemcpy(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return CQ_OK;
+}
+
+static int create_impl(int natom, const double* xyz, const int* Z, int nshell, const int* shell_atom,
+                       const int* shell_L, const int* shell_nprim, const double* exps,
+                       const double* coefs, cq_basis* b)
+{
+    CQ_CUDA(cudaGetDevice(&b->device));
+    b->natom = natom;
+    b->nsh = nshell;
+    b->xyz.assign(xyz, xyz + 3 * natom);
+    b->Z.assign(Z, Z + natom);
+    b->L.assign(shell_L, shell_L + nshell);
+    b->nprim.assign(shell_nprim, shell_nprim + nshell);
+    b->atom.assign(shell_atom, shell_atom + nshell);
+    b->poff.resize(nshell);
+    b->bfo.resize(nshell + 1);
+    int np = 0, nbf = 0;
+    for (int s = 0; s < nshell; ++s) {
+        b->poff[s] = np;
+        b->bfo[s] = nbf;
+        np += b->nprim[s];
+        nbf += ncart(b->L[s]);
+    }
+    b->bfo[nshell] = nbf;
+    b->nbf = nbf;
+    b->exps.assign(exps, exps + np);
+    b->coefs.assign(coefs, coefs + np);
+
+    // ---- shell pairs, grouped by class and sorted by primitive count
+    std::vector<double> ctr(3 * nshell);
+    for (int s = 0; s < nshell; ++s)
+        for (int x = 0; x < 3; ++x) ctr[3 * s + x] = xyz[3 * b->atom[s] + x];
+    std::vector<std::vector<PairHdr>> bycls(NPC);
+    for (int a = 0; a < nshell; ++a)
+        for (int c = 0; c <= a; ++c) {
+            int s1 = a, s2 = c;
+            if (b->L[s1] < b->L[s2]) std::swap(s1, s2);
+            PairHdr h;
+            h.a = s1; h.b = s2;
+            h.bfa = b->bfo[s1]; h.bfb = b->bfo[s2];
+            h.nprim = b->nprim[s1] * b->nprim[s2];
+            h.poff = 0;
+            for (int x = 0; x < 3; ++x) h.AB[x] = ctr[3 * s1 + x] - ctr[3 * s2 + x];
+            bycls[pc_of(b->L[s1], b->L[s2])].push_back(h);
+        }
+    b->pairs.clear();
+    for (int c = 0; c < NPC; ++c) {
+        auto& v = bycls[c];
+        std::stable_sort(v.begin(), v.end(), [](const PairHdr& x, const PairHdr& y) {
+            if (x.nprim != y.nprim) return x.nprim > y.nprim;
+            if (x.a != y.a) return x.a < y.a;
+            return x.b < y.b;
+        });
+        b->cls_off[c] = (int)b->pairs.size();
+        b->pairs.insert(b->pairs.end(), v.begin(), v.end());
+    }
+    b->cls_off[NPC] = (int)b->pairs.size();
+    b->npair = (int)b->pairs.size();
+    int q = 0;
+    for (auto& h : b->pairs) { h.poff = q; q += h.nprim; }
+    b->nprim_pairs = q;
+
+    // ---- warp tasks per quartet class: (bra, first ket candidate), costliest first
+    b->task_off.assign(NQC + 1, 0);
+    std::vector<int2> tasks;
+    for (int X = 0, qc = 0; X < NPC; ++X)
+        for (int Y = 0; Y <= X; ++Y, ++qc) {
+            b->task_off[qc] = (int)tasks.size();
+            std::vector<std::pair<double, int2>> tv;
+            for (int i = b->cls_off[X]; i < b->cls_off[X + 1]; ++i) {
+                const int jb = b->cls_off[Y], je = (X == Y) ? i + 1 : b->cls_off[Y + 1];
+                for (int j0 = jb; j0 < je; j0 += JK_RANGE) {
+                    double cost = 0.0;
+                    for (int j = j0; j < std::min(je, j0 + JK_RANGE); ++j) cost += b->pairs[j].nprim;
+                    tv.push_back({cost * b->pairs[i].nprim, make_int2(i, j0)});
+                }
+            }
+            std::stable_sort(tv.begin(), tv.end(),
+                             [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+                                 return x.first > y.first;
+                             });
+            for (auto& t : tv) tasks.push_back(t.second);
+        }
+    b->task_off[NQC] = (int)tasks.size();
+
+    // ---- device copies
+    int rc;
+    std::vector<double> axyz(xyz, xyz + 3 * natom), zc(Z, Z + natom);
+    if ((rc = upload(&b->d_ctr, ctr))) return rc;
+    if ((rc = upload(&b->d_L, b->L))) return rc;
+    if ((rc = upload(&b->d_nprim, b->nprim))) return rc;
+    if ((rc = upload(&b->d_poff, b->poff))) return rc;
+    if ((rc = upload(&b->d_bfo, b->bfo))) return rc;
+    if ((rc = upload(&b->d_exps, b->exps))) return rc;
+    if ((rc = upload(&b->d_pairs, b->pairs))) return rc;
+    if ((rc = upload(&b->d_tasks, tasks))) return rc;
+    if ((rc = upload(&b->d_axyz, axyz))) return rc;
+    if ((rc = upload(&b->d_Z, zc))) return rc;
+    if ((rc = dalloc(&b->d_coef, np))) return rc;
+    if ((rc = dalloc(&b->d_scale, nbf))) return rc;
+    if ((rc = dalloc(&b->d_prims, b->nprim_pairs))) return rc;
+    if ((rc = dalloc(&b->d_primsf, b->nprim_pairs))) return rc;
+    if ((rc = dalloc(&b->d_boys, (size_t)BOYS_NT * BOYS_D_COLS))) return rc;
+    if ((rc = dalloc(&b->d_boysf, (size_t)BOYS_NT * BOYS_F_COLS))) return rc;
+    if ((rc = dalloc(&b->d_Qf, b->npair))) return rc;
+    if ((rc = dalloc(&b->d_Qd, b->npair))) return rc;
+    if ((rc = dalloc(&b->d_cnt, 4))) return rc;
+    {
+        std::vector<double> coefs_raw(coefs, coefs + np);
+        double* d_raw = nullptr;
+        if ((rc = upload(&d_raw, coefs_raw))) return rc;
+        normalize_kernel<<<(nshell + 127) / 128, 128>>>(nshell, b->d_L, b->d_nprim, b->d_poff, b->d_exps,
+                                                      d_raw, b->d_coef);
+        cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(d_raw);
+        CQ_CUDA(e);
+    }
+    scale_kernel<<<(nshell + 127) / 128, 128>>>(nshell, b->d_L, b->d_bfo, b->d_scale);
+    boys_table_kernel<<<(BOYS_NT + 127) / 128, 128>>>(b->d_boys, b->d_boysf);
+    pair_prep_kernel<<<(b->npair + 127) / 128, 128>>>(b->npair, b->d_pairs, b->d_ctr, b->d_nprim,
+                                                      b->d_poff, b->d_exps, b->d_coef, b->d_prims,
+                                                      b->d_primsf);
+    CQ_CUDA(cudaGetLastError());
+    CQ_CUDA(cudaEventCreate(&b->ev0));
+    CQ_CUDA(cudaEventCreate(&b->ev1));
+    rc = cq_schwarz(b, nullptr, nullptr);
+    if (rc) return rc;
+    CQ_CUDA(cudaDeviceSynchronize());
+    return CQ_OK;
+}
+
+extern "C" int cq_basis_create(int natom, const double* xyz, const int* Z, int nshell,
+                               const int* shell_atom, const int* shell_L, const int* shell_nprim,
+                               const double* exps, const double* coefs, cq_basis** out)
+{
+    if (!out) { set_error("cq_basis_create: out is NULL"); return CQ_ERR_INVALID_ARG; }
+    *out = nullptr;
+    if (natom <= 0 || nshell <= 0 || !xyz || !Z || !shell_atom || !shell_L || !shell_nprim || !exps ||
+        !coefs) {
+        set_error("cq_basis_create: empty basis or NULL argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    int np = 0;
+    for (int s = 0; s < nshell; ++s) {
+        if (shell_L[s] < 0 || shell_L[s] > LMAX) {
+            set_error("cq_basis_create: shell angular momentum outside 0..2");
+            return CQ_ERR_INVALID_ARG;
+        }
+        if (shell_nprim[s] < 1 || shell_nprim[s] > MAX_PRIM) {
+            set_error("cq_basis_create: primitive count outside 1..16");
+            return CQ_ERR_INVALID_ARG;
+        }
+        if (shell_atom[s] < 0 || shell_atom[s] >= natom) {
+            set_error("cq_basis_create: shell_atom out of range");
+            return CQ_ERR_INVALID_ARG;
+        }
+        np += shell_nprim[s];
+    }
+    for (int k = 0; k < np; ++k)
+        if (!(exps[k] > 0.0) || !std::isfinite(exps[k]) || !std::isfinite(coefs[k])) {
+            set_error("cq_basis_create: exponents must be positive and finite");
+            return CQ_ERR_INVALID_ARG;
+        }
+    for (int k = 0; k < 3 * natom; ++k)
+        if (!std::isfinite(xyz[k])) {
+            set_error("cq_basis_create: non-finite coordinate");
+            return CQ_ERR_INVALID_ARG;
+        }
+    cq_basis* b = new cq_basis();
+    int rc = create_impl(natom, xyz, Z, nshell, shell_atom, shell_L, shell_nprim, exps, coefs, b);
+    if (rc) { free_basis(b); return rc; }
+    *out = b;
+    return CQ_OK;
+}
+
+extern "C" void cq_basis_destroy(cq_basis* b)
+{
+    if (b) cudaDeviceSynchronize();
+    free_basis(b);
+}
+
+extern "C" int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npair)
+{
+    if (!b) { set_error("cq_basis_info: NULL basis"); return CQ_ERR_INVALID_ARG; }
+    if (nbf) *nbf = b->nbf;
+    if (nshell) *nshell = b->nsh;
+    if (npair) *npair = b->npair;
+    return CQ_OK;
+}
+
+__global__ void schwarz_square_kernel(int npair, const PairHdr* pairs, const double* Qd, int nsh, double* Q)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npair) return;
+    const PairHdr h = pairs[p];
+    Q[(size_t)h.a * nsh + h.b] = Qd[p];
+    Q[(size_t)h.b * nsh + h.a] = Qd[p];
+}
+
+extern "C" int cq_schwarz(cq_basis* b, double* Q, void* stream)
+{
+    if (!b) { set_error("cq_schwarz: NULL basis"); return CQ_ERR_INVALID_ARG; }
+    cudaStream_t s = (cudaStream_t)stream;
+    JKArgs a;
+    memset(&a, 0, sizeof a);
+    a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
+    a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
+    for (int c = 0; c < NPC; ++c) {
+        const int beg = b->cls_off[c], end = b->cls_off[c + 1];
+        if (end > beg) SCHWARZ_LAUNCH[c](a, beg, end, b->d_Qf, b->d_Qd, s);
+    }
+    CQ_CUDA(cudaGetLastError());
+    if (Q) {
+        schwarz_square_kernel<<<(b->npair + 127) / 128, 128, 0, s>>>(b->npair, b->d_pairs, b->d_Qd, b->nsh, Q);
+        CQ_CUDA(cudaGetLastError());
+    }
+    return CQ_OK;
+}
+
+extern "C" int cq_nuclear_repulsion(const cq_basis* b, double* E)
+{
+    if (!b || !E) { set_error("cq_nuclear_repulsion: NULL argument"); return CQ_ERR_INVALID_ARG; }
+    double e = 0.0;
+    for (int i = 0; i < b->natom; ++i)
+        for (int j = 0; j < i; ++j) {
+            const double dx = b->xyz[3 * i] - b->xyz[3 * j], dy = b->xyz[3 * i + 1] - b->xyz[3 * j + 1],
+                         dz = b->xyz[3 * i + 2] - b->xyz[3 * j + 2];
+            e += (double)b->Z[i] * b->Z[j] / std::sqrt(dx * dx + dy * dy + dz * dz);
+        }
+    *E = e;
+    return CQ_OK;
+}

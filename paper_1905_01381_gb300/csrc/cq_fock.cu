@@ -1,0 +1,198 @@
+// Direct Fock build J, K <- P (Eq. 2c_fock), over unique shell quartets.
+//
+// Conventions.  The integral kernels evaluate (ab|cd) for the x^L
+// normalisation of every shell; the Cartesian component factors s_m are
+// applied to the density on the way in (P'_{mn} = s_m s_n P_{mn}) and to J
+// and K on the way out.  Each unique quartet (a>=b, c>=d, ab>=cd) carries the
+// degeneracy factor sdeg = (1/2 if a==b)(1/2 if c==d)(1/2 if ab==cd) and adds
+//     J'_ab += 2 sdeg (ab|cd) D_cd,   J'_cd += 2 sdeg (ab|cd) D_ab,
+//     K'_ac += sdeg (ab|cd) D_bd,  K'_ad += sdeg (ab|cd) D_bc,
+//     K'_bc += sdeg (ab|cd) D_ad,  K'_bd += sdeg (ab|cd) D_ac,
+// after which J = J' + J'^T and K = K' + K'^T for a symmetric density or
+// K = K' - K'^T for an antisymmetric one (the eight index permutations of a
+// real integral folded into four accumulations and one transpose).
+//
+// A Hermitian P = P_R + i P_I has P_R symmetric and P_I antisymmetric, so
+// J[P] = J[P_R] and K[P] = K[P_R] + i K[P_I]; the Pauli case applies this
+// to P^0..P^3 (eight real K matrices, J from Re P^0).
+#include <cstring>
+
+#include "cq_internal.h"
+#include "cq_jk.cuh"
+
+namespace cq {
+
+// P (layout by kind) -> nk scaled real matrices.
+__global__ void density_prep_kernel(int kind, int n, const double* __restrict__ P,
+                                    const double* __restrict__ sc, double* __restrict__ Dp)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const int r = (int)(i / n), c = (int)(i % n);
+    const double f = sc[r] * sc[c];
+    if (kind == CQ_DENS_REAL_SYM) {
+        Dp[i] = f * P[i];
+    } else if (kind == CQ_DENS_COMPLEX_HERM) {
+        Dp[i] = f * P[2 * i];
+        Dp[nn + i] = f * P[2 * i + 1];
+    } else {
+        for (int I = 0; I < 4; ++I) {
+            Dp[(2 * I) * nn + i] = f * P[2 * (I * nn + i)];
+            Dp[(2 * I + 1) * nn + i] = f * P[2 * (I * nn + i) + 1];
+        }
+    }
+}
+
+// Shell-block maxima of |P'| over all nk matrices.
+__global__ void dmax_kernel(int nsh, int n, int nk, const int* __restrict__ bfo, const double* __restrict__ Dp,
+                            float* __restrict__ Dmax)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= nsh * nsh) return;
+    const int a = p / nsh, b = p % nsh;
+    double m = 0.0;
+    for (int q = 0; q < nk; ++q)
+        for (int i = bfo[a]; i < bfo[a + 1]; ++i)
+            for (int j = bfo[b]; j < bfo[b + 1]; ++j) m = fmax(m, fabs(Dp[(size_t)q * n * n + (size_t)i * n + j]));
+    Dmax[p] = (float)m * 1.0000005f;
+}
+
+// J = s s (J' + J'^T); K_q = s s (K'_q +/- K'_q^T) written in the output layout.
+__global__ void finalize_kernel(int kind, int n, const double* __restrict__ sc, const double* __restrict__ Jp,
+                                const double* __restrict__ Kp, double* __restrict__ J, double* __restrict__ K,
+                                int want_j, int want_k)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    const int r = (int)(i / n), c = (int)(i % n);
+    const size_t t = (size_t)c * n + r;
+    const double f = sc[r] * sc[c];
+    if (want_j) J[i] = f * (Jp[i] + Jp[t]);
+    if (!want_k) return;
+    if (kind == CQ_DENS_REAL_SYM) {
+        K[i] = f * (Kp[i] + Kp[t]);
+    } else if (kind == CQ_DENS_COMPLEX_HERM) {
+        K[2 * i] = f * (Kp[i] + Kp[t]);
+        K[2 * i + 1] = f * (Kp[nn + i] - Kp[nn + t]);
+    } else {
+        for (int I = 0; I < 4; ++I) {
+            const double* Kr = Kp + (2 * I) * nn;
+            const double* Ki = Kp + (2 * I + 1) * nn;
+            K[2 * (I * nn + i)] = f * (Kr[i] + Kr[t]);
+            K[2 * (I * nn + i) + 1] = f * (Ki[i] - Ki[t]);
+        }
+    }
+}
+
+static int nk_of(int kind) { return kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8; }
+
+int ensure_scratch(cq_basis* b, int nk)
+{
+    if (nk <= b->nk_cap) return CQ_OK;
+    const size_t nn = (size_t)b->nbf * b->nbf;
+    if (b->d_Dp) cudaFree(b->d_Dp);
+    if (b->d_Kp) cudaFree(b->d_Kp);
+    b->d_Dp = b->d_Kp = nullptr;
+    int rc;
+    if ((rc = dalloc(&b->d_Dp, nn * nk))) return rc;
+    if ((rc = dalloc(&b->d_Kp, nn * nk))) return rc;
+    if (!b->d_Jp && (rc = dalloc(&b->d_Jp, nn))) return rc;
+    if (!b->d_Dmax && (rc = dalloc(&b->d_Dmax, (size_t)b->nsh * b->nsh))) return rc;
+    b->nk_cap = nk;
+    return CQ_OK;
+}
+
+}  // namespace cq
+
+using namespace cq;
+
+extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
+                             const cq_fock_opts* opts, cq_fock_stats* stats, void* stream)
+{
+    if (!b || !P) { set_error("cq_fock_build: NULL basis or density"); return CQ_ERR_INVALID_ARG; }
+    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_PAULI4) {
+        set_error("cq_fock_build: unknown density kind");
+        return CQ_ERR_INVALID_ARG;
+    }
+    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1};
+    if (opts) o = *opts;
+    if ((o.want_J && !J) || (o.want_K && !K)) {
+        set_error("cq_fock_build: requested output pointer is NULL");
+        return CQ_ERR_INVALID_ARG;
+    }
+    if (o.prec != CQ_PREC_FP64 && o.prec != CQ_PREC_MIXED) {
+        set_error("cq_fock_build: unknown precision mode");
+        return CQ_ERR_INVALID_ARG;
+    }
+    if (!(o.schwarz_tol >= 0.0) || !(o.mixed_tol >= 0.0)) {
+        set_error("cq_fock_build: negative threshold");
+        return CQ_ERR_INVALID_ARG;
+    }
+    const int nk = nk_of(kind);
+    int rc = ensure_scratch(b, nk);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n = b->nbf;
+    const size_t nn = (size_t)n * n;
+    const int nb = (int)((nn + 255) / 256);
+    if (stats) CQ_CUDA(cudaEventRecord(b->ev0, s));
+    density_prep_kernel<<<nb, 256, 0, s>>>(kind, n, (const double*)P, b->d_scale, b->d_Dp);
+    dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, b->d_Dp, b->d_Dmax);
+    CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, 4 * sizeof(unsigned long long), s));
+    JKArgs a;
+    memset(&a, 0, sizeof a);
+    a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
+    a.Q = b->d_Qf; a.Dmax = b->d_Dmax; a.nsh = b->nsh;
+    a.tau = (float)o.schwarz_tol;
+    a.tau_mixed = (float)o.mixed_tol;
+    a.D = b->d_Dp; a.nk = nk; a.nbf = n;
+    a.want_j = o.want_J; a.want_k = o.want_K;
+    a.J = b->d_Jp; a.K = b->d_Kp;
+    a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
+    // heaviest classes first
+    static const int order[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
+    for (int oi = 0; oi < NQC; ++oi) {
+        const int qc = order[oi];
+        int X = 0;
+        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+        const int Y = qc - X * (X + 1) / 2;
+        a.tasks = b->d_tasks + b->task_off[qc];
+        a.ntasks = b->task_off[qc + 1] - b->task_off[qc];
+        if (a.ntasks == 0) continue;
+        a.ket_end = b->cls_off[Y + 1];
+        a.same_class = (X == Y);
+        if (o.prec == CQ_PREC_FP64) {
+            a.prec_sel = 0;
+            a.counters = b->d_cnt;
+            JK_LAUNCH[qc](a, 0, s);
+        } else {
+            a.prec_sel = 1;
+            a.counters = b->d_cnt;
+            JK_LAUNCH[qc](a, 0, s);
+            a.prec_sel = 2;
+            a.counters = b->d_cnt + 2;
+            JK_LAUNCH[qc](a, 1, s);
+        }
+    }
+    CQ_CUDA(cudaGetLastError());
+    finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, b->d_Jp, b->d_Kp, J, (double*)K, o.want_J, o.want_K);
+    CQ_CUDA(cudaGetLastError());
+    if (stats) {
+        CQ_CUDA(cudaEventRecord(b->ev1, s));
+        unsigned long long c[4];
+        CQ_CUDA(cudaMemcpyAsync(c, b->d_cnt, sizeof c, cudaMemcpyDeviceToHost, s));
+        CQ_CUDA(cudaStreamSynchronize(s));
+        float ms = 0.f;
+        CQ_CUDA(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+        stats->quartets_fp64 = c[0];
+        stats->prim_fp64 = c[1];
+        stats->quartets_fp32 = c[2];
+        stats->prim_fp32 = c[3];
+        stats->ms = ms;
+    }
+    return CQ_OK;
+}

@@ -1,0 +1,89 @@
+// Internal host-side state of the Fock-build library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cq.h"
+#include "cq_common.cuh"
+
+namespace cq {
+
+struct JKArgs;
+
+// pair classes (la, lb), la >= lb: 00 10 11 20 21 22
+constexpr int NPC = 6;
+constexpr int NQC = 21;   // (bra class X) >= (ket class Y)
+inline int pc_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+extern const int PC_L[NPC][2];
+
+using LaunchJK = void (*)(const JKArgs&, int fp32, cudaStream_t);
+using LaunchSchwarz = void (*)(const JKArgs&, int, int, float*, double*, cudaStream_t);
+extern const LaunchJK JK_LAUNCH[NQC];          // index: X*(X+1)/2 + Y
+extern const LaunchSchwarz SCHWARZ_LAUNCH[NPC];
+
+void set_error(const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define CQ_CUDA(call)                                         \
+    do {                                                      \
+        cudaError_t _e = (call);                              \
+        if (_e != cudaSuccess) return cq::cuda_fail(_e, #call); \
+    } while (0)
+
+template <typename T>
+int dalloc(T** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? CQ_ERR_OOM : CQ_ERR_CUDA;
+    }
+    return CQ_OK;
+}
+
+}  // namespace cq
+
+struct cq_basis {
+    int device = 0;
+    int natom = 0, nsh = 0, nbf = 0, npair = 0, nprim_pairs = 0;
+    std::vector<double> xyz;
+    std::vector<int> Z;
+    std::vector<int> L, nprim, poff, atom, bfo;
+    std::vector<double> exps, coefs;
+    // pair classes
+    int cls_off[cq::NPC + 1] = {0};
+    std::vector<cq::PairHdr> pairs;
+    // tasks per quartet class
+    std::vector<int> task_off;   // NQC + 1
+    // device data
+    double* d_boys = nullptr;
+    float* d_boysf = nullptr;
+    cq::PairHdr* d_pairs = nullptr;
+    cq::PrimPair* d_prims = nullptr;
+    cq::PrimPairF* d_primsf = nullptr;
+    int2* d_tasks = nullptr;
+    float* d_Qf = nullptr;
+    double* d_Qd = nullptr;
+    double* d_scale = nullptr;     // per-function Cartesian component factor
+    double* d_ctr = nullptr;       // shell centres
+    int* d_L = nullptr;
+    int* d_nprim = nullptr;
+    int* d_poff = nullptr;
+    int* d_bfo = nullptr;
+    double* d_exps = nullptr;
+    double* d_coef = nullptr;      // normalised (x^L component) coefficients
+    double* d_axyz = nullptr;
+    double* d_Z = nullptr;
+    // per-build scratch (grown on demand)
+    int nk_cap = 0;
+    double* d_Dp = nullptr;        // nk scaled densities
+    double* d_Jp = nullptr;        // J'
+    double* d_Kp = nullptr;        // nk K'
+    float* d_Dmax = nullptr;       // nsh x nsh
+    unsigned long long* d_cnt = nullptr;  // 4 counters
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};

@@ -1,0 +1,301 @@
+// J/K kernel template: one warp per (bra shell pair, range of ket shell
+// pairs), one lane per contracted shell quartet.  Included by the generated
+// per-class translation units after the class's EriClass specialisation.
+#pragma once
+#include "cq_common.cuh"
+
+namespace cq {
+
+constexpr int JK_THREADS = 128;   // 4 warps per CTA
+constexpr int JK_RANGE = 64;      // ket candidates per warp task
+
+struct JKArgs {
+    const PairHdr* pairs;
+    const PrimPair* prims;
+    const PrimPairF* primsf;
+    const int2* tasks;            // (bra pair, first ket candidate)
+    int ntasks;
+    int ket_end;                  // end of the ket class range (exclusive)
+    int same_class;               // bra and ket class equal: kets j <= bra
+    const float* Q;               // Schwarz factor per pair
+    const float* Dmax;            // nsh x nsh block maxima of |P| (all components)
+    int nsh;
+    float tau;                    // screening threshold
+    float tau_mixed;              // precision split
+    int prec_sel;                 // 0: every surviving quartet; 1: bound >= tau_mixed; 2: bound < tau_mixed
+    const double* D;              // nk scaled density matrices, nbf x nbf each
+    int nk;
+    int nbf;
+    int want_j, want_k;
+    double* J;                    // J' accumulator nbf x nbf
+    double* K;                    // K' accumulators nk x nbf x nbf
+    const double* boys_d;
+    const float* boys_f;
+    unsigned long long* counters; // [0] quartets, [1] primitive quartets
+};
+
+template <typename R>
+__device__ __forceinline__ R ldR(const double* p) { return (R)__ldg(p); }
+
+template <typename R>
+__device__ __forceinline__ void load_prim(const PrimPair* pd, const PrimPairF* pf, int i,
+                                          PrimPairT<R>& o);
+
+template <>
+__device__ __forceinline__ void load_prim<double>(const PrimPair* pd, const PrimPairF*, int i,
+                                                  PrimPairT<double>& o)
+{
+    const double* s = reinterpret_cast<const double*>(pd + i);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
+}
+
+template <>
+__device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPairF* pf, int i,
+                                                 PrimPairT<float>& o)
+{
+    const float* s = reinterpret_cast<const float*>(pf + i);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
+}
+
+// Contracted quartet (ab|cd) over the primitive pairs of bra and ket.
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void eri_quartet(const PairHdr& B, const PairHdr& K, const JKArgs& a,
+                                            R* __restrict__ I)
+{
+    using C = EriClass<LA, LB, LC, LD>;
+    constexpr int L = LA + LB + LC + LD;
+    R acc[C::NACC];
+#pragma unroll
+    for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
+    const R* boys_tab;
+    if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
+    for (int ip = 0; ip < B.nprim; ++ip) {
+        PrimPairT<R> bp;
+        load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+        for (int jp = 0; jp < K.nprim; ++jp) {
+            PrimPairT<R> kp;
+            load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+            PrimQuartet<R> q;
+            const R s = bp.zeta + kp.zeta;
+            const R rs = rsqrt_r(s);
+            const R is = rs * rs;
+            const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
+            const R roz = kp.zeta * is;   // rho/zeta = eta/(zeta+eta)
+            const R roe = bp.zeta * is;   // rho/eta  = zeta/(zeta+eta)
+            const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
+            R F[L + 1];
+            boys<L>(T, F, boys_tab);
+            const R pref = bp.K * kp.K * rs;
+#pragma unroll
+            for (int m = 0; m <= L; ++m) q.S[m] = pref * F[m];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) { q.PA[x] = bp.PA[x]; q.QC[x] = kp.PA[x]; }
+            q.WP[0] = -roz * PQx; q.WP[1] = -roz * PQy; q.WP[2] = -roz * PQz;
+            q.WQ[0] = roe * PQx;  q.WQ[1] = roe * PQy;  q.WQ[2] = roe * PQz;
+            q.oo2z = bp.oo2z; q.oo2e = kp.oo2z; q.oo2ze = R(0.5) * is;
+            q.roz = roz; q.roe = roe;
+            C::template prim<R>(q, acc);
+        }
+    }
+    R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
+    R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
+    C::template hrr<R>(acc, ABv, CDv, I);
+}
+
+__device__ __forceinline__ float dmax6(const float* Dm, int nsh, int a, int b, int c, int d)
+{
+    float m = fmaxf(__ldg(Dm + a * nsh + b), __ldg(Dm + c * nsh + d));
+    m = fmaxf(m, fmaxf(__ldg(Dm + a * nsh + c), __ldg(Dm + a * nsh + d)));
+    m = fmaxf(m, fmaxf(__ldg(Dm + b * nsh + c), __ldg(Dm + b * nsh + d)));
+    return m;
+}
+
+// Contract one quartet's integral block with the density blocks and add the
+// resulting J'/K' blocks (see the Fock-build notes in cq_fock.cu for the
+// half-accumulation convention: J = J' + J'^T, K = K' +/- K'^T).
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const R* __restrict__ I,
+                                       R sdeg, const JKArgs& a, double* __restrict__ jab)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    const int n = a.nbf;
+    const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+    if (a.want_j) {
+        const double* D0 = a.D;
+        R dab[NA * NB], dcd[NC * ND], jcd[NC * ND];
+#pragma unroll
+        for (int m = 0; m < NA; ++m)
+#pragma unroll
+            for (int k = 0; k < NB; ++k) dab[m * NB + k] = ldR<R>(D0 + (size_t)(fa + m) * n + fb + k);
+#pragma unroll
+        for (int l = 0; l < NC; ++l)
+#pragma unroll
+            for (int s = 0; s < ND; ++s) {
+                dcd[l * ND + s] = ldR<R>(D0 + (size_t)(fc + l) * n + fd + s);
+                jcd[l * ND + s] = R(0);
+            }
+#pragma unroll
+        for (int mn = 0; mn < NA * NB; ++mn) {
+            R t = R(0);
+#pragma unroll
+            for (int ls = 0; ls < NC * ND; ++ls) {
+                const R v = I[mn * NC * ND + ls];
+                t = fma(v, dcd[ls], t);
+                jcd[ls] = fma(v, dab[mn], jcd[ls]);
+            }
+            jab[mn] = fma(2.0 * (double)sdeg, (double)t, jab[mn]);
+        }
+        const double f = 2.0 * (double)sdeg;
+#pragma unroll
+        for (int l = 0; l < NC; ++l)
+#pragma unroll
+            for (int s = 0; s < ND; ++s)
+                atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)jcd[l * ND + s]);
+    }
+    if (a.want_k) {
+#pragma unroll 1
+        for (int q = 0; q < a.nk; ++q) {
+            const double* Dq = a.D + (size_t)q * n * n;
+            double* Kq = a.K + (size_t)q * n * n;
+            R dbd[NB * ND], dbc[NB * NC], dad[NA * ND], dac[NA * NC];
+            R kac[NA * NC], kad[NA * ND], kbc[NB * NC], kbd[NB * ND];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+#pragma unroll
+                for (int s = 0; s < ND; ++s) { dbd[k * ND + s] = ldR<R>(Dq + (size_t)(fb + k) * n + fd + s); kbd[k * ND + s] = R(0); }
+#pragma unroll
+                for (int l = 0; l < NC; ++l) { dbc[k * NC + l] = ldR<R>(Dq + (size_t)(fb + k) * n + fc + l); kbc[k * NC + l] = R(0); }
+            }
+#pragma unroll
+            for (int m = 0; m < NA; ++m) {
+#pragma unroll
+                for (int s = 0; s < ND; ++s) { dad[m * ND + s] = ldR<R>(Dq + (size_t)(fa + m) * n + fd + s); kad[m * ND + s] = R(0); }
+#pragma unroll
+                for (int l = 0; l < NC; ++l) { dac[m * NC + l] = ldR<R>(Dq + (size_t)(fa + m) * n + fc + l); kac[m * NC + l] = R(0); }
+            }
+#pragma unroll
+            for (int m = 0; m < NA; ++m)
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+#pragma unroll
+                    for (int l = 0; l < NC; ++l)
+#pragma unroll
+                        for (int s = 0; s < ND; ++s) {
+                            const R v = I[((m * NB + k) * NC + l) * ND + s];
+                            kac[m * NC + l] = fma(v, dbd[k * ND + s], kac[m * NC + l]);
+                            kad[m * ND + s] = fma(v, dbc[k * NC + l], kad[m * ND + s]);
+                            kbc[k * NC + l] = fma(v, dad[m * ND + s], kbc[k * NC + l]);
+                            kbd[k * ND + s] = fma(v, dac[m * NC + l], kbd[k * ND + s]);
+                        }
+            const double f = (double)sdeg;
+#pragma unroll
+            for (int m = 0; m < NA; ++m) {
+#pragma unroll
+                for (int l = 0; l < NC; ++l) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)kac[m * NC + l]);
+#pragma unroll
+                for (int s = 0; s < ND; ++s) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)kad[m * ND + s]);
+            }
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+#pragma unroll
+                for (int l = 0; l < NC; ++l) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)kbc[k * NC + l]);
+#pragma unroll
+                for (int s = 0; s < ND; ++s) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)kbd[k * ND + s]);
+            }
+        }
+    }
+}
+
+template <int LA, int LB, int LC, int LD, typename R>
+__global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB);
+    using C = EriClass<LA, LB, LC, LD>;
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * JK_THREADS + threadIdx.x) >> 5;
+    if (w >= a.ntasks) return;
+    const int2 t = a.tasks[w];
+    const int ib = t.x;
+    const int jend = min(t.y + JK_RANGE, a.same_class ? ib + 1 : a.ket_end);
+    const PairHdr B = a.pairs[ib];
+    const float Qb = __ldg(a.Q + ib);
+    double jab[NA * NB];
+#pragma unroll
+    for (int i = 0; i < NA * NB; ++i) jab[i] = 0.0;
+    unsigned long long nq = 0, np = 0;
+    for (int j0 = t.y; j0 < jend; j0 += 32) {
+        const int j = j0 + lane;
+        bool on = j < jend;
+        PairHdr K;
+        if (on) {
+            K = a.pairs[j];
+            const float bound = Qb * __ldg(a.Q + j) * dmax6(a.Dmax, a.nsh, B.a, B.b, K.a, K.b);
+            on = bound >= a.tau;
+            if (a.prec_sel == 1) on = on && bound >= a.tau_mixed;
+            else if (a.prec_sel == 2) on = on && bound < a.tau_mixed;
+        }
+        if (on) {
+            R I[C::N];
+            eri_quartet<LA, LB, LC, LD, R>(B, K, a, I);
+            R sdeg = R(1);
+            if (B.a == B.b) sdeg *= R(0.5);
+            if (K.a == K.b) sdeg *= R(0.5);
+            if (j == ib) sdeg *= R(0.5);
+            digest<LA, LB, LC, LD, R>(B, K, I, sdeg, a, jab);
+            nq += 1;
+            np += (unsigned long long)B.nprim * K.nprim;
+        }
+    }
+    // warp reduction of the bra J' block, one writer per warp
+    if (a.want_j) {
+#pragma unroll
+        for (int i = 0; i < NA * NB; ++i) {
+            double v = jab[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0 && v != 0.0) {
+                const int m = i / NB, k = i % NB;
+                atomicAdd(a.J + (size_t)(B.bfa + m) * a.nbf + B.bfb + k, v);
+            }
+        }
+    }
+    if (a.counters) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nq += __shfl_xor_sync(0xffffffffu, nq, o);
+            np += __shfl_xor_sync(0xffffffffu, np, o);
+        }
+        if (lane == 0 && nq) {
+            atomicAdd(a.counters + 0, nq);
+            atomicAdd(a.counters + 1, np);
+        }
+    }
+}
+
+// Schwarz factors of the pairs [begin, end) of class (LA LB): one thread per
+// pair, (ab|ab) in FP64.
+template <int LA, int LB>
+__global__ void schwarz_kernel(const JKArgs a, int begin, int end, float* Qf, double* Qd)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB);
+    const int p = begin + blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= end) return;
+    const PairHdr B = a.pairs[p];
+    double I[EriClass<LA, LB, LA, LB>::N];
+    eri_quartet<LA, LB, LA, LB, double>(B, B, a, I);
+    double mx = 0.0;
+#pragma unroll
+    for (int m = 0; m < NA; ++m)
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const double v = fabs(I[((m * NB + k) * NA + m) * NB + k]);
+            mx = v > mx ? v : mx;
+        }
+    const double q = sqrt(mx);
+    Qd[p] = q;
+    Qf[p] = (float)q * 1.0000005f;   // round up: a bound must not shrink in FP32
+}
+
+}  // namespace cq

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every symbol include/cq.h declares;
+host-side argument validation returns documented status codes.  CPU only
+(no compute calls)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def libcq():
+    import paper_1905_01381_gb300 as cq
+    cq.build()
+    return cq.lib()
+
+
+def declared_symbols():
+    out = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            out += re.findall(r"\b(cq_[a-z0-9_]+)\s*\(", txt)
+    return sorted(set(out))
+
+
+def test_every_declared_symbol_is_exported(libcq):
+    syms = declared_symbols()
+    assert "cq_fock_build" in syms and "cq_basis_create" in syms
+    for s in syms:
+        assert hasattr(libcq, s), s
+
+
+def test_invalid_basis_rejected_on_host(libcq):
+    dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+    xyz = np.zeros(3)
+    Z = np.array([1], np.int32)
+    atom = np.array([0], np.int32)
+    nprim = np.array([1], np.int32)
+    ex = np.array([1.0])
+    co = np.array([1.0])
+    h = ctypes.c_void_p()
+    for L, e in [(3, 1.0), (0, -1.0), (-1, 1.0)]:
+        Ls = np.array([L], np.int32)
+        exv = np.array([e])
+        rc = libcq.cq_basis_create(1, xyz.ctypes.data_as(dp), Z.ctypes.data_as(ip), 1,
+                                   atom.ctypes.data_as(ip), Ls.ctypes.data_as(ip),
+                                   nprim.ctypes.data_as(ip), exv.ctypes.data_as(dp),
+                                   co.ctypes.data_as(dp), ctypes.byref(h))
+        assert rc == -1
+        assert b"" != libcq.cq_last_error()
+    bad_atom = np.array([5], np.int32)
+    rc = libcq.cq_basis_create(1, xyz.ctypes.data_as(dp), Z.ctypes.data_as(ip), 1,
+                               bad_atom.ctypes.data_as(ip), np.array([0], np.int32).ctypes.data_as(ip),
+                               nprim.ctypes.data_as(ip), ex.ctypes.data_as(dp), co.ctypes.data_as(dp),
+                               ctypes.byref(h))
+    assert rc == -1
+    rc = libcq.cq_fock_build(None, 0, None, None, None, None, None, None)
+    assert rc == -1
