@@ -1,0 +1,362 @@
+"""Benchmark: direct J+K Fock builds on the 16-atom RT-TDHF workload.
+
+Workload: seeded 16-atom O/H cluster (6 O, 10 H; min distance 1.7 bohr),
+even-tempered s,p,d basis (210 Cartesian functions, contraction depth 1-6),
+complex-Hermitian density from 29 random orthonormal orbitals -- the density
+a real-time TDHF step contracts.  One step = one J+K build (every class
+kernel, density preparation and finalisation), Schwarz threshold 1e-14.
+
+Headline `value`: mixed-precision builds/s (FP32 for quartets whose Schwarz x
+density bound is below mixed_tol, everything accumulated in FP64), with the
+energy error against the all-FP64 GPU build checked in the same run
+(|dE| <= 1e-6 Eh).  The all-FP64 rate is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
+  python bench.py --impl reference ...   # the CPU oracle on the same workload
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "J+K Fock builds/s & ERI quartets/s; mixed vs FP64 GPU at |dE|<=1e-6 Eh"
+WORKLOAD = "rt16: 16-atom O6H10 cluster, 210 Cartesian s,p,d functions, complex-Hermitian P (29 occ)"
+MIXED_TOL = 1e-5
+NOCC = 29
+
+
+def workload():
+    mol, bas = synth.workload_rt16()
+    n = bas.nbf
+    P = synth.density(n, NOCC, 5, complex_=True)
+    return mol, bas, P
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rk = int(os.environ.get("RANK", "0"))
+    lr = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rk, lr
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # 256 MiB write, larger than the 129 MB L2
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    ws, rk, _ = dist_env()
+    if rk != 0:
+        return 0
+    import oracle
+    oracle.build()
+    mol, bas, P = workload()
+    ob = oracle.OBasis(mol, bas)
+    npair = ob.nsh * (ob.nsh + 1) // 2
+    total = npair * (npair + 1) // 2
+    nthreads = oracle.nthreads_default()
+    stride = args.ref_stride
+    Ds = [P.real, P.imag]
+    oracle.jk_sample(ob, Ds, stride * 8, 0, nthreads)   # warm-up (small)
+    times, nqs = [], []
+    for k in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        _, _, nq = oracle.jk_sample(ob, Ds, stride, k % stride, nthreads)
+        dt = time.perf_counter() - t
+        if k >= args.warmup:
+            times.append(dt); nqs.append(nq)
+    qps = sum(nqs) / sum(times)
+    builds = qps / total
+    line = {"impl": "reference", "metric": METRIC, "value": builds, "unit": "builds/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / builds, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nbf": int(ob.nbf), "unique_shell_quartets": total},
+            "quartets_per_s": qps,
+            "cpu_baseline": {"value": builds, "unit": "builds/s", "cores": nthreads, "kind": "oracle",
+                             "sample": f"per step: bra shell pairs p % {stride} == k of the unique "
+                                       f"quartet loop ({total} quartets per full build); builds/s = "
+                                       f"quartets/s / {total}"},
+            "e2e": {"value": builds, "unit": "builds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(seconds: float):
+    import oracle
+    oracle.build()
+    mol, bas, P = workload()
+    ob = oracle.OBasis(mol, bas)
+    npair = ob.nsh * (ob.nsh + 1) // 2
+    total = npair * (npair + 1) // 2
+    nthreads = oracle.nthreads_default()
+    Ds = [P.real, P.imag]
+    stride = 400
+    t = time.perf_counter()
+    _, _, nq = oracle.jk_sample(ob, Ds, stride, 3, nthreads)
+    dt = time.perf_counter() - t
+    # grow the sample to roughly `seconds`
+    stride2 = max(1, int(stride * dt / max(seconds, 1e-3)))
+    t = time.perf_counter()
+    _, _, nq = oracle.jk_sample(ob, Ds, stride2, 1, nthreads)
+    dt = time.perf_counter() - t
+    qps = nq / dt
+    return {"value": qps / total, "unit": "builds/s", "cores": nthreads, "kind": "oracle",
+            "sample": f"bra shell pairs p % {stride2} == 1 of the unique-quartet loop: {nq} of {total} "
+                      f"shell quartets in {dt:.1f} s ({qps:.3g} quartets/s), scaled to one build",
+            "quartets_per_s": qps}
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1905_01381_gb300 as cq
+    from paper_1905_01381_gb300 import flops as fl
+
+    ws, rk, lr = dist_env()
+    torch.cuda.set_device(lr)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    cq.build() if rk == 0 or ws == 1 else None
+    if ws > 1:
+        dist.barrier()
+    mol, bas, Ph = workload()
+    b = cq.Basis(mol, bas)
+    n = b.nbf
+    stream = torch.cuda.current_stream()
+    P = torch.as_tensor(Ph, device="cuda")
+    prec = cq.CQ_PREC_MIXED if args.prec == "mixed" else cq.CQ_PREC_FP64
+    J = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    K = torch.empty((n, n), dtype=torch.complex128, device="cuda")
+    flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # ---- accuracy of the timed mode against the all-FP64 build (same run)
+    J64, K64 = b.fock_build(P)
+    Jm, Km = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL)
+    dF = 2 * (Jm - J64).to(torch.complex128) - (Km - K64)
+    dE = float(abs(torch.sum(dF * P.T).real.item()))
+    dJ = float((Jm - J64).abs().max().item())
+    dK = float((Km - K64).abs().max().item())
+
+    def build():
+        b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, J=J, K=K)
+
+    for _ in range(args.warmup):
+        build()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(lr) as clk:
+        for i in range(args.steps):
+            flush_l2(flush)
+            ev[i][0].record(stream)
+            build()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(c) for a, c in ev]
+    tot_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([tot_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = t.item()
+    value = ws * args.steps / (tot_ms * 1e-3)
+
+    # ---- per-class profile (one extra build, events around each class kernel)
+    b.profile(True)
+    _, _, st = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, J=J, K=K, stats=True)
+    cls = b.class_stats()
+    b.profile(False)
+    quartets = st["quartets_fp64"] + st["quartets_fp32"]
+    nk = 2
+    tot_flops64 = tot_flops32 = 0.0
+    dom = None
+    for key, v in cls.items():
+        X, Y = cq.QUARTET_CLASSES[v["qc"]]
+        f = fl.class_flops(X, Y, v["quartets"], v["prims"], nk)
+        v["flops"] = f
+        if v["fp32"]:
+            tot_flops32 += f
+        else:
+            tot_flops64 += f
+        if dom is None or v["ms"] > cls[dom]["ms"]:
+            dom = key
+    peak64 = cq.peak_fma(False)
+    peak32 = cq.peak_fma(True)
+    dv = cls[dom]
+    dom_peak = peak32 if dv["fp32"] else peak64
+    achieved = dv["flops"] / (dv["ms"] * 1e-3)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            src = open(os.path.join(ROOT, "paper_1905_01381_gb300", "csrc", "cq_jk.cuh")).read()
+            import hashlib
+            if tj.get("kernel") == dom and tj.get("cq_jk_sha1") == hashlib.sha1(src.encode()).hexdigest():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # ---- FP64-only rate (reported beside the headline)
+    fp64_rate = None
+    if prec != cq.CQ_PREC_FP64:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrep = max(1, min(3, args.steps))
+        tms = 0.0
+        for _ in range(nrep):
+            flush_l2(flush)
+            e0.record(stream)
+            b.fock_build(P, J=J, K=K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms += e0.elapsed_time(e1)
+        fp64_rate = nrep / (tms * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    Ph_pin = torch.from_numpy(Ph).pin_memory()
+    Jh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    Kh = torch.empty((n, n), dtype=torch.complex128).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrep = max(1, min(3, args.steps))
+    e0.record(stream)
+    for _ in range(nrep):
+        Pd = Ph_pin.to("cuda", non_blocking=True)
+        Jd, Kd = b.fock_build(Pd, prec=prec, mixed_tol=MIXED_TOL)
+        Jh.copy_(Jd, non_blocking=True)
+        Kh.copy_(Kd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e = ws * nrep / (e0.elapsed_time(e1) * 1e-3)
+
+    launches_per_build = 4 + sum(1 for v in cls.values())
+    out = None
+    if rk == 0:
+        out = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64+f32" if prec != cq.CQ_PREC_FP64 else "f64", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "nbf": n, "precision": args.prec, "mixed_tol": MIXED_TOL,
+                          "schwarz_tol": 1e-14, "l2": "flushed (256 MiB write) between timed steps",
+                          "parallelism": f"replicas x{ws}"},
+               "quartets_per_s": value * quartets,
+               "quartets_per_build": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"]},
+               "prim_quartets_per_build": {"fp64": st["prim_fp64"], "fp32": st["prim_fp32"]},
+               "fp64_builds_per_s": fp64_rate if fp64_rate is not None else value,
+               "accuracy_vs_fp64_gpu": {"dE_Eh": dE, "max_dJ": dJ, "max_dK": dK},
+               "gflops_per_build": {"fp64": tot_flops64 * 1e-9, "fp32": tot_flops32 * 1e-9},
+               "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved * 1e-12,
+                            "peak": dom_peak * 1e-12, "unit": "TFLOP/s", "frac": achieved / dom_peak,
+                            "traffic": traffic,
+                            "peak_source": "measured FMA-chain peak in this run (cq_peak_fma), "
+                                           f"fp64 {peak64 * 1e-12:.3f} / fp32 {peak32 * 1e-12:.2f} TFLOP/s"},
+               "class_ms": {k: round(v["ms"], 3) for k, v in sorted(cls.items(), key=lambda kv: -kv[1]["ms"])},
+               "e2e": {"value": e2e, "unit": "builds/s", "h2d_bytes_per_step": n * n * 16,
+                       "d2h_bytes_per_step": n * n * 8 + n * n * 16},
+               "gpu_launches": launches_per_build * args.steps,
+               "clocks": clk.summary()}
+    b.close()
+    if ws > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rk == 0 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds) if ws == 1 else None
+    if rk == 0:
+        print(json.dumps(out))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-stride", type=int, default=150)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

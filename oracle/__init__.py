@@ -188,3 +188,17 @@ def jk_elements(ob, Ds, mu, nu, nthreads: int | None = None):
     lib().or_jk_elements(*ob.args(), len(Ds), _d(D), ne, _i(mu), _i(nu), _d(Jo), _d(Ko),
                          nthreads if nthreads is not None else nthreads_default())
     return Jo, Ko
+
+
+def jk_sample(ob, Ds, stride: int, offset: int = 0, nthreads: int | None = None):
+    """J'/K' partial sums over the bra shell pairs p % stride == offset;
+    returns (J, K, shell quartets visited).  Timing support only."""
+    Ds = [np.ascontiguousarray(D, dtype=np.float64) for D in Ds]
+    D = np.ascontiguousarray(np.stack(Ds))
+    J = np.zeros_like(D)
+    K = np.zeros_like(D)
+    f = lib().or_jk_sample
+    f.restype = ctypes.c_long
+    nq = f(*ob.args(), len(Ds), _d(D), _d(J), _d(K),
+           nthreads if nthreads is not None else nthreads_default(), stride, offset)
+    return J, K, int(nq)

@@ -478,9 +478,9 @@ static inline void apply_tuple(int n, int nd, const double *D, double *J,
 
 /* J and K for nd general real densities (each nbf x nbf row-major).
  * Visits every permutationally unique function quartet once. */
-void or_jk(int nsh, const double *ctr, const int *L, const int *np,
+static long jk_impl(int nsh, const double *ctr, const int *L, const int *np,
            const int *poff, const double *ex, const double *co, int nd,
-           const double *D, double *J, double *K, int nthreads)
+           const double *D, double *J, double *K, int nthreads, int stride, int offset)
 {
     Basis B;
     basis_init(&B, nsh, ctr, L, np, poff, ex, co);
@@ -488,6 +488,7 @@ void or_jk(int nsh, const double *ctr, const int *L, const int *np,
     memset(J, 0, sizeof(double) * nn);
     memset(K, 0, sizeof(double) * nn);
     int npair = nsh * (nsh + 1) / 2;
+    long nq = 0;
     int *pa = (int *)malloc(sizeof(int) * npair), *pb = (int *)malloc(sizeof(int) * npair);
     for (int a = 0, p = 0; a < nsh; ++a)
         for (int b = 0; b <= a; ++b, ++p) { pa[p] = a; pb[p] = b; }
@@ -499,8 +500,10 @@ void or_jk(int nsh, const double *ctr, const int *L, const int *np,
         double *Jt = (double *)calloc(nn, sizeof(double));
         double *Kt = (double *)calloc(nn, sizeof(double));
         double *blk = (double *)malloc(sizeof(double) * 1296);
-#pragma omp for schedule(dynamic, 1)
+#pragma omp for schedule(dynamic, 1) reduction(+ : nq)
         for (int p1 = npair - 1; p1 >= 0; --p1) {
+            if (p1 % stride != offset) continue;
+            nq += p1 + 1;
             int a = pa[p1], b = pb[p1];
             for (int p2 = 0; p2 <= p1; ++p2) {
                 int c = pa[p2], d = pb[p2];
@@ -540,6 +543,24 @@ void or_jk(int nsh, const double *ctr, const int *L, const int *np,
     }
     free(pa); free(pb);
     basis_free(&B);
+    return nq;
+}
+
+void or_jk(int nsh, const double *ctr, const int *L, const int *np,
+           const int *poff, const double *ex, const double *co, int nd,
+           const double *D, double *J, double *K, int nthreads)
+{
+    jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, 1, 0);
+}
+
+/* The same loop restricted to bra shell pairs p with p % stride == offset
+ * (a deterministic sample of the unique shell quartets, used only to time
+ * the oracle on large cases).  Returns the number of shell quartets visited. */
+long or_jk_sample(int nsh, const double *ctr, const int *L, const int *np,
+                  const int *poff, const double *ex, const double *co, int nd,
+                  const double *D, double *J, double *K, int nthreads, int stride, int offset)
+{
+    return jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, stride, offset);
 }
 
 /* Selected elements straight from the definition, for sampling large cases:

@@ -59,6 +59,11 @@ def lib():
                                     ctypes.POINTER(FockStats), vp]
         L.cq_nuclear_repulsion.argtypes = [vp, dp]
         L.cq_last_error.restype = ctypes.c_char_p
+        L.cq_fock_profile.argtypes = [vp, ctypes.c_int]
+        L.cq_fock_class_stats.argtypes = [vp, ctypes.c_int, ctypes.c_int, dp,
+                                          ctypes.POINTER(ctypes.c_ulonglong),
+                                          ctypes.POINTER(ctypes.c_ulonglong)]
+        L.cq_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp]
         _lib = L
     return _lib
 
@@ -77,6 +82,17 @@ def _stream_ptr(stream):
 
 def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
+QUARTET_CLASSES = [(X, Y) for X in range(6) for Y in range(X + 1)]
+
+
+def peak_fma(fp32: bool, iters: int = 20000, stream=None) -> float:
+    """Measured FMA throughput in FLOP/s (an FMA counts 2)."""
+    v = ctypes.c_double()
+    check(lib().cq_peak_fma(int(fp32), iters, ctypes.byref(v), _stream_ptr(stream)), "cq_peak_fma")
+    return v.value
 
 
 class Basis:
@@ -159,3 +175,21 @@ class Basis:
             return J, K, {"quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32,
                           "prim_fp64": st.prim_fp64, "prim_fp32": st.prim_fp32, "ms": st.ms}
         return J, K
+
+    def profile(self, enable: bool = True):
+        check(lib().cq_fock_profile(self.h, int(enable)), "cq_fock_profile")
+
+    def class_stats(self):
+        """Per-class (time ms, quartets, primitive quartets) of the last build."""
+        out = {}
+        for qc, (X, Y) in enumerate(QUARTET_CLASSES):
+            for p in (0, 1):
+                ms = ctypes.c_double()
+                nq, npq = ctypes.c_ulonglong(), ctypes.c_ulonglong()
+                check(lib().cq_fock_class_stats(self.h, qc, p, ctypes.byref(ms), ctypes.byref(nq),
+                                                ctypes.byref(npq)), "cq_fock_class_stats")
+                if nq.value or ms.value:
+                    key = f"({PAIR_CLASSES[X]}|{PAIR_CLASSES[Y]})" + ("f32" if p else "f64")
+                    out[key] = {"qc": qc, "fp32": p, "ms": ms.value, "quartets": nq.value,
+                                "prims": npq.value}
+        return out

@@ -19,10 +19,15 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "--expt-relaxed-constexpr", "-Xptxas=-warn-spills", "-I", CSRC, "-I", GEN,
                   "-I", os.path.join(os.path.dirname(HERE), "include")]
-HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu"]
+HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu", "cq_peaks.cu"]
 LIBS = ["-lcublas", "-lcusolver"]
 
 PCS = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
+
+# lanes per contracted quartet (G) for each class: classes with few quartets
+# and expensive primitive quartets split the primitive loop over more lanes
+LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
+         "2120": 2, "2111": 2, "2210": 2, "1111": 2}
 
 
 def qclasses():
@@ -39,41 +44,50 @@ def gen_sources():
     sys.path.pop(0)
     stats = gen_eri.main(GEN)
     tus = []
-    for qc, (X, Y) in enumerate(qclasses()):
-        la, lb, lc, ld = X[0], X[1], Y[0], Y[1]
-        cls = f"{la}{lb}{lc}{ld}"
-        src = [f"// generated by build.py: class ({cls})",
-               '#include "cq_common.cuh"',
-               "namespace cq {",
-               f'#include "eri_{cls}.cuh"',
-               "}",
-               '#include "cq_jk.cuh"',
-               "namespace cq {",
-               f"void launch_jk_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
-               "{",
-               "    const int blocks = (a.ntasks * 32 + JK_THREADS - 1) / JK_THREADS;",
-               "    if (blocks == 0) return;",
-               f"    if (fp32) jk_kernel<{la}, {lb}, {lc}, {ld}, float><<<blocks, JK_THREADS, 0, s>>>(a);",
-               f"    else jk_kernel<{la}, {lb}, {lc}, {ld}, double><<<blocks, JK_THREADS, 0, s>>>(a);",
-               "}"]
-        if X == Y:
-            src += [f"void launch_schwarz_{la}{lb}(const JKArgs& a, int begin, int end, float* Qf, double* Qd, cudaStream_t s)",
-                    "{",
-                    "    const int n = end - begin;",
-                    "    if (n <= 0) return;",
-                    f"    schwarz_kernel<{la}, {lb}><<<(n + 63) / 64, 64, 0, s>>>(a, begin, end, Qf, Qd);",
-                    "}"]
-        src.append("}  // namespace cq")
-        path = os.path.join(GEN, f"cls_{cls}.cu")
-        text = "\n".join(src) + "\n"
+
+    def write(path, lines):
+        text = "\n".join(lines) + "\n"
         if not os.path.exists(path) or open(path).read() != text:
             with open(path, "w") as fh:
                 fh.write(text)
         tus.append(path)
+
+    for qc, (X, Y) in enumerate(qclasses()):
+        la, lb, lc, ld = X[0], X[1], Y[0], Y[1]
+        cls = f"{la}{lb}{lc}{ld}"
+        G = LANES.get(cls, 1)
+        head = [f"// generated by build.py: class ({cls})",
+                '#include "cq_common.cuh"',
+                "namespace cq {",
+                f'#include "eri_{cls}.cuh"',
+                "}",
+                '#include "cq_jk.cuh"',
+                "namespace cq {"]
+        for R, tag in (("double", "f64"), ("float", "f32")):
+            src = head + [
+                f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
+                "{",
+                "    const int blocks = (a.ntasks * 32 + JK_THREADS - 1) / JK_THREADS;",
+                "    if (blocks == 0) return;",
+                f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<blocks, JK_THREADS, 0, s>>>(a);",
+                "}"]
+            if X == Y and tag == "f64":
+                src += [f"void launch_schwarz_{la}{lb}(const JKArgs& a, int begin, int end, float* Qf, double* Qd, cudaStream_t s)",
+                        "{",
+                        "    const int n = end - begin;",
+                        "    if (n <= 0) return;",
+                        f"    schwarz_kernel<{la}, {lb}><<<(n + 63) / 64, 64, 0, s>>>(a, begin, end, Qf, Qd);",
+                        "}"]
+            src.append("}  // namespace cq")
+            write(os.path.join(GEN, f"cls_{cls}_{tag}.cu"), src)
     # dispatch table
     d = ['#include "cq_internal.h"', "namespace cq {"]
     for (X, Y) in qclasses():
-        d.append(f"void launch_jk_{X[0]}{X[1]}{Y[0]}{Y[1]}(const JKArgs&, int, cudaStream_t);")
+        c = f"{X[0]}{X[1]}{Y[0]}{Y[1]}"
+        d.append(f"void launch_jk_{c}_f64(const JKArgs&, cudaStream_t);")
+        d.append(f"void launch_jk_{c}_f32(const JKArgs&, cudaStream_t);")
+        d.append(f"static void launch_jk_{c}(const JKArgs& a, int fp32, cudaStream_t s) "
+                 f"{{ if (fp32) launch_jk_{c}_f32(a, s); else launch_jk_{c}_f64(a, s); }}")
     for X in PCS:
         d.append(f"void launch_schwarz_{X[0]}{X[1]}(const JKArgs&, int, int, float*, double*, cudaStream_t);")
     d.append("const LaunchJK JK_LAUNCH[NQC] = {" +
@@ -81,12 +95,7 @@ def gen_sources():
     d.append("const LaunchSchwarz SCHWARZ_LAUNCH[NPC] = {" +
              ", ".join(f"launch_schwarz_{X[0]}{X[1]}" for X in PCS) + "};")
     d.append("}  // namespace cq")
-    path = os.path.join(GEN, "cq_dispatch.cu")
-    text = "\n".join(d) + "\n"
-    if not os.path.exists(path) or open(path).read() != text:
-        with open(path, "w") as fh:
-            fh.write(text)
-    tus.append(path)
+    write(os.path.join(GEN, "cq_dispatch.cu"), d)
     return tus, stats
 
 
@@ -119,7 +128,8 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
     srcs = [os.path.join(CSRC, s) for s in HAND_SOURCES] + tus
     # heaviest TUs first so the parallel build finishes early
     srcs.sort(key=lambda s: -os.path.getsize(s) if "cls_" not in s else
-              -os.path.getsize(os.path.join(GEN, "eri_" + os.path.basename(s)[4:8] + ".cuh")))
+              -os.path.getsize(os.path.join(GEN, "eri_" + os.path.basename(s)[4:8] + ".cuh"))
+              * (2 if s.endswith("_f64.cu") else 1))
     jobs = jobs or max(1, os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(jobs) as ex:
         res = list(ex.map(lambda s: _compile(s, verbose), srcs))

@@ -149,6 +149,10 @@ static void free_basis(cq_basis* b)
         if (p) cudaFree(p);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < 2; ++p)
+            for (int e = 0; e < 2; ++e)
+                if (b->pev[q][p][e]) cudaEventDestroy(b->pev[q][p][e]);
     delete b;
 }
 
@@ -265,7 +269,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     if ((rc = dalloc(&b->d_boysf, (size_t)BOYS_NT * BOYS_F_COLS))) return rc;
     if ((rc = dalloc(&b->d_Qf, b->npair))) return rc;
     if ((rc = dalloc(&b->d_Qd, b->npair))) return rc;
-    if ((rc = dalloc(&b->d_cnt, 4))) return rc;
+    if ((rc = dalloc(&b->d_cnt, 4 + 4 * NQC))) return rc;
     {
         std::vector<double> coefs_raw(coefs, coefs + np);
         double* d_raw = nullptr;

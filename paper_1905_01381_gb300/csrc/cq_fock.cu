@@ -86,6 +86,15 @@ __global__ void finalize_kernel(int kind, int n, const double* __restrict__ sc, 
     }
 }
 
+__global__ void counter_total_kernel(unsigned long long* c)
+{
+    if (threadIdx.x < 4) {
+        unsigned long long t = 0;
+        for (int q = 0; q < NQC; ++q) t += c[4 + 4 * q + threadIdx.x];
+        c[threadIdx.x] = t;   // [0] fp64 quartets [1] fp64 prims [2] fp32 quartets [3] fp32 prims
+    }
+}
+
 static int nk_of(int kind) { return kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8; }
 
 int ensure_scratch(cq_basis* b, int nk)
@@ -142,7 +151,8 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, b->d_Dp, b->d_Dmax);
     CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
-    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, 4 * sizeof(unsigned long long), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 4 * NQC) * sizeof(unsigned long long), s));
+    if (b->profile) memset(b->pev_used, 0, sizeof b->pev_used);
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
@@ -165,20 +175,23 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
         if (a.ntasks == 0) continue;
         a.ket_end = b->cls_off[Y + 1];
         a.same_class = (X == Y);
-        if (o.prec == CQ_PREC_FP64) {
-            a.prec_sel = 0;
-            a.counters = b->d_cnt;
-            JK_LAUNCH[qc](a, 0, s);
-        } else {
-            a.prec_sel = 1;
-            a.counters = b->d_cnt;
-            JK_LAUNCH[qc](a, 0, s);
-            a.prec_sel = 2;
-            a.counters = b->d_cnt + 2;
-            JK_LAUNCH[qc](a, 1, s);
+        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
+            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
+            a.counters = b->d_cnt + 4 + 4 * qc + 2 * pp;
+            if (b->profile) {
+                for (int e = 0; e < 2; ++e)
+                    if (!b->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&b->pev[qc][pp][e]));
+                CQ_CUDA(cudaEventRecord(b->pev[qc][pp][0], s));
+            }
+            JK_LAUNCH[qc](a, pp, s);
+            if (b->profile) {
+                CQ_CUDA(cudaEventRecord(b->pev[qc][pp][1], s));
+                b->pev_used[qc][pp] = true;
+            }
         }
     }
     CQ_CUDA(cudaGetLastError());
+    counter_total_kernel<<<1, 32, 0, s>>>(b->d_cnt);
     finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, b->d_Jp, b->d_Kp, J, (double*)K, o.want_J, o.want_K);
     CQ_CUDA(cudaGetLastError());
     if (stats) {
@@ -193,6 +206,34 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
         stats->quartets_fp32 = c[2];
         stats->prim_fp32 = c[3];
         stats->ms = ms;
+    }
+    return CQ_OK;
+}
+
+extern "C" int cq_fock_profile(cq_basis* b, int enable)
+{
+    if (!b) { set_error("cq_fock_profile: NULL basis"); return CQ_ERR_INVALID_ARG; }
+    b->profile = enable ? 1 : 0;
+    return CQ_OK;
+}
+
+extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, unsigned long long* quartets,
+                                   unsigned long long* prims)
+{
+    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1) {
+        set_error("cq_fock_class_stats: bad argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    CQ_CUDA(cudaDeviceSynchronize());
+    unsigned long long c[2];
+    CQ_CUDA(cudaMemcpy(c, b->d_cnt + 4 + 4 * qc + 2 * fp32, sizeof c, cudaMemcpyDeviceToHost));
+    if (quartets) *quartets = c[0];
+    if (prims) *prims = c[1];
+    if (ms) {
+        float t = 0.f;
+        if (b->profile && b->pev_used[qc][fp32])
+            CQ_CUDA(cudaEventElapsedTime(&t, b->pev[qc][fp32][0], b->pev[qc][fp32][1]));
+        *ms = t;
     }
     return CQ_OK;
 }

@@ -84,6 +84,11 @@ struct cq_basis {
     double* d_Jp = nullptr;        // J'
     double* d_Kp = nullptr;        // nk K'
     float* d_Dmax = nullptr;       // nsh x nsh
-    unsigned long long* d_cnt = nullptr;  // 4 counters
+    unsigned long long* d_cnt = nullptr;  // 4 totals + per class/precision (quartets, prims)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // optional per-class profile of the last build
+    int profile = 0;
+    cudaEvent_t pev[cq::NQC][2][2] = {};
+    bool pev_used[cq::NQC][2] = {};
+    unsigned long long pcnt[cq::NQC][2][2] = {};
 };

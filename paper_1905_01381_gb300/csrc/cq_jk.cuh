@@ -59,13 +59,42 @@ __device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPair
     for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
 }
 
+// One primitive quartet: prefactor, Boys values and the class's vertical
+// recurrence, accumulated into acc.
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void prim_quartet(const PrimPairT<R>& bp, const PrimPairT<R>& kp,
+                                             const R* __restrict__ boys_tab, R* __restrict__ acc)
+{
+    using C = EriClass<LA, LB, LC, LD>;
+    constexpr int L = LA + LB + LC + LD;
+    PrimQuartet<R> q;
+    const R s = bp.zeta + kp.zeta;
+    const R rs = rsqrt_r(s);
+    const R is = rs * rs;
+    const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
+    const R roz = kp.zeta * is;   // rho/zeta = eta/(zeta+eta)
+    const R roe = bp.zeta * is;   // rho/eta  = zeta/(zeta+eta)
+    const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
+    R F[L + 1];
+    boys<L>(T, F, boys_tab);
+    const R pref = bp.K * kp.K * rs;
+#pragma unroll
+    for (int m = 0; m <= L; ++m) q.S[m] = pref * F[m];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) { q.PA[x] = bp.PA[x]; q.QC[x] = kp.PA[x]; }
+    q.WP[0] = -roz * PQx; q.WP[1] = -roz * PQy; q.WP[2] = -roz * PQz;
+    q.WQ[0] = roe * PQx;  q.WQ[1] = roe * PQy;  q.WQ[2] = roe * PQz;
+    q.oo2z = bp.oo2z; q.oo2e = kp.oo2z; q.oo2ze = R(0.5) * is;
+    q.roz = roz; q.roe = roe;
+    C::template prim<R>(q, acc);
+}
+
 // Contracted quartet (ab|cd) over the primitive pairs of bra and ket.
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void eri_quartet(const PairHdr& B, const PairHdr& K, const JKArgs& a,
                                             R* __restrict__ I)
 {
     using C = EriClass<LA, LB, LC, LD>;
-    constexpr int L = LA + LB + LC + LD;
     R acc[C::NACC];
 #pragma unroll
     for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
@@ -77,26 +106,7 @@ __device__ __forceinline__ void eri_quartet(const PairHdr& B, const PairHdr& K, 
         for (int jp = 0; jp < K.nprim; ++jp) {
             PrimPairT<R> kp;
             load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-            PrimQuartet<R> q;
-            const R s = bp.zeta + kp.zeta;
-            const R rs = rsqrt_r(s);
-            const R is = rs * rs;
-            const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
-            const R roz = kp.zeta * is;   // rho/zeta = eta/(zeta+eta)
-            const R roe = bp.zeta * is;   // rho/eta  = zeta/(zeta+eta)
-            const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
-            R F[L + 1];
-            boys<L>(T, F, boys_tab);
-            const R pref = bp.K * kp.K * rs;
-#pragma unroll
-            for (int m = 0; m <= L; ++m) q.S[m] = pref * F[m];
-#pragma unroll
-            for (int x = 0; x < 3; ++x) { q.PA[x] = bp.PA[x]; q.QC[x] = kp.PA[x]; }
-            q.WP[0] = -roz * PQx; q.WP[1] = -roz * PQy; q.WP[2] = -roz * PQz;
-            q.WQ[0] = roe * PQx;  q.WQ[1] = roe * PQy;  q.WQ[2] = roe * PQz;
-            q.oo2z = bp.oo2z; q.oo2e = kp.oo2z; q.oo2ze = R(0.5) * is;
-            q.roz = roz; q.roe = roe;
-            C::template prim<R>(q, acc);
+            prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
         }
     }
     R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
@@ -208,44 +218,239 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
     }
 }
 
-template <int LA, int LB, int LC, int LD, typename R>
+// Digestion of the integral subset owned by one lane of a G-lane group
+// (bra function pairs mn = sub, sub+G, ...).  Adds the lane's partial J'_cd
+// and K' blocks to jcd / kblk (zeroed by the caller) and its J'_ab part to jab.
+template <int LA, int LB, int LC, int LD, typename R, int G>
+__device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, const R* __restrict__ I,
+                                            R sdeg, const JKArgs& a, int q, int sub, double* __restrict__ jab,
+                                            R* __restrict__ jcd, R* __restrict__ kblk)
+{
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NCD = NC * ND;
+    R* kac = kblk;
+    R* kad = kac + NA * NC;
+    R* kbc = kad + NA * ND;
+    R* kbd = kbc + NB * NC;
+    const int n = a.nbf;
+    const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+    const double* Dq = a.D + (size_t)q * n * n;
+    if (q == 0 && a.want_j) {
+        R dcd[NCD];
+#pragma unroll
+        for (int l = 0; l < NC; ++l)
+#pragma unroll
+            for (int s = 0; s < ND; ++s) dcd[l * ND + s] = ldR<R>(Dq + (size_t)(fc + l) * n + fd + s);
+#pragma unroll 1
+        for (int mn = sub; mn < NA * NB; mn += G) {
+            const int m = mn / NB, k = mn - (mn / NB) * NB;
+            const R dab = ldR<R>(Dq + (size_t)(fa + m) * n + fb + k);
+            R t = R(0);
+#pragma unroll
+            for (int ls = 0; ls < NCD; ++ls) {
+                const R v = I[mn * NCD + ls];
+                t = fma(v, dcd[ls], t);
+                jcd[ls] = fma(v, dab, jcd[ls]);
+            }
+            jab[mn] = fma(2.0 * (double)sdeg, (double)t, jab[mn]);
+        }
+    }
+    if (a.want_k) {
+#pragma unroll 1
+        for (int mn = sub; mn < NA * NB; mn += G) {
+            const int m = mn / NB, k = mn - (mn / NB) * NB;
+            R dbd[ND], dbc[NC], dad[ND], dac[NC];
+#pragma unroll
+            for (int s = 0; s < ND; ++s) {
+                dbd[s] = ldR<R>(Dq + (size_t)(fb + k) * n + fd + s);
+                dad[s] = ldR<R>(Dq + (size_t)(fa + m) * n + fd + s);
+            }
+#pragma unroll
+            for (int l = 0; l < NC; ++l) {
+                dbc[l] = ldR<R>(Dq + (size_t)(fb + k) * n + fc + l);
+                dac[l] = ldR<R>(Dq + (size_t)(fa + m) * n + fc + l);
+            }
+#pragma unroll
+            for (int l = 0; l < NC; ++l)
+#pragma unroll
+                for (int s = 0; s < ND; ++s) {
+                    const R v = I[mn * NCD + l * ND + s];
+                    kac[m * NC + l] = fma(v, dbd[s], kac[m * NC + l]);
+                    kad[m * ND + s] = fma(v, dbc[l], kad[m * ND + s]);
+                    kbc[k * NC + l] = fma(v, dad[s], kbc[k * NC + l]);
+                    kbd[k * ND + s] = fma(v, dac[l], kbd[k * ND + s]);
+                }
+        }
+    }
+}
+
+template <typename T, int G>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Lane-group variant: a group of G lanes evaluates one contracted quartet,
+// its lanes splitting the primitive quartets; accumulators and digested
+// blocks are summed across the group with shuffles.  Kets that survive
+// screening (and belong to this kernel's precision) are compacted through a
+// per-warp queue in shared memory so that no group idles on a rejected ket.
+template <int LA, int LB, int LC, int LD, typename R, int G>
 __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
 {
-    constexpr int NA = ncart(LA), NB = ncart(LB);
+    constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
+    constexpr int NKB = NA * NC + NA * ND + NB * NC + NB * ND;
+    constexpr int S = 32 / G;
     using C = EriClass<LA, LB, LC, LD>;
-    const int lane = threadIdx.x & 31;
-    const int w = (blockIdx.x * JK_THREADS + threadIdx.x) >> 5;
+    __shared__ int queue[JK_THREADS / 32][64];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int grp = lane / G, sub = lane - (lane / G) * G;
+    const int w = blockIdx.x * (JK_THREADS / 32) + wib;
     if (w >= a.ntasks) return;
     const int2 t = a.tasks[w];
     const int ib = t.x;
     const int jend = min(t.y + JK_RANGE, a.same_class ? ib + 1 : a.ket_end);
     const PairHdr B = a.pairs[ib];
     const float Qb = __ldg(a.Q + ib);
+    const float* Dm = a.Dmax;
+    const int ns = a.nsh;
+    const float dab_max = __ldg(Dm + B.a * ns + B.b);
     double jab[NA * NB];
 #pragma unroll
     for (int i = 0; i < NA * NB; ++i) jab[i] = 0.0;
+    int* qw = queue[wib];
+    int qn = 0;
+    int c0 = t.y;
     unsigned long long nq = 0, np = 0;
-    for (int j0 = t.y; j0 < jend; j0 += 32) {
-        const int j = j0 + lane;
-        bool on = j < jend;
-        PairHdr K;
-        if (on) {
-            K = a.pairs[j];
-            const float bound = Qb * __ldg(a.Q + j) * dmax6(a.Dmax, a.nsh, B.a, B.b, K.a, K.b);
-            on = bound >= a.tau;
-            if (a.prec_sel == 1) on = on && bound >= a.tau_mixed;
-            else if (a.prec_sel == 2) on = on && bound < a.tau_mixed;
+    while (true) {
+        while (qn < S && c0 < jend) {
+            const int j = c0 + lane;
+            bool sel = false;
+            if (j < jend) {
+                const int kc = __ldg(&a.pairs[j].a), kd = __ldg(&a.pairs[j].b);
+                float m = fmaxf(dab_max, __ldg(Dm + kc * ns + kd));
+                m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + kc), __ldg(Dm + B.a * ns + kd)));
+                m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + kc), __ldg(Dm + B.b * ns + kd)));
+                const float bound = Qb * __ldg(a.Q + j) * m;
+                sel = bound >= a.tau;
+                if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
+                else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, sel);
+            if (sel) qw[qn + __popc(msk & ((1u << lane) - 1u))] = j;
+            qn += __popc(msk);
+            c0 += 32;
+            __syncwarp();
         }
+        if (qn == 0) break;
+        const int cnt = min(S, qn);
+        const bool on = grp < cnt;
+        const int j = on ? qw[grp] : ib;
+        const int rem = qn - cnt;
+        const int mv = lane < rem ? qw[cnt + lane] : 0;
+        __syncwarp();
+        if (lane < rem) qw[lane] = mv;
+        __syncwarp();
+        qn = rem;
+
+        const PairHdr K = a.pairs[j];
+        R acc[C::NACC];
+#pragma unroll
+        for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
         if (on) {
+            const R* boys_tab;
+            if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
+            const int nkp = K.nprim, tot = B.nprim * K.nprim;
+            for (int pq = sub; pq < tot; pq += G) {
+                const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
+                PrimPairT<R> bp, kp;
+                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
+            }
+            if (sub == 0) { nq += 1; np += (unsigned long long)tot; }
+        }
+        if constexpr (G > 1) {
+#pragma unroll
+            for (int i = 0; i < C::NACC; ++i) acc[i] = group_sum<R, G>(acc[i]);
+        }
+        R sdeg = R(1);
+        if (B.a == B.b) sdeg *= R(0.5);
+        if (K.a == K.b) sdeg *= R(0.5);
+        if (j == ib) sdeg *= R(0.5);
+        if constexpr (G == 1) {
+            if (on) {
+                R I[C::N];
+                R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
+                R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
+                C::template hrr<R>(acc, ABv, CDv, I);
+                digest<LA, LB, LC, LD, R>(B, K, I, sdeg, a, jab);
+            }
+        } else {
             R I[C::N];
-            eri_quartet<LA, LB, LC, LD, R>(B, K, a, I);
-            R sdeg = R(1);
-            if (B.a == B.b) sdeg *= R(0.5);
-            if (K.a == K.b) sdeg *= R(0.5);
-            if (j == ib) sdeg *= R(0.5);
-            digest<LA, LB, LC, LD, R>(B, K, I, sdeg, a, jab);
-            nq += 1;
-            np += (unsigned long long)B.nprim * K.nprim;
+            if (on) {
+                R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
+                R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
+                C::template hrr<R>(acc, ABv, CDv, I);
+            }
+            const int n = a.nbf;
+            const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+#pragma unroll 1
+            for (int q = 0; q < a.nk; ++q) {
+                if (q > 0 && !a.want_k) break;
+                R jcd[NC * ND], kb[NKB];
+#pragma unroll
+                for (int i = 0; i < NC * ND; ++i) jcd[i] = R(0);
+#pragma unroll
+                for (int i = 0; i < NKB; ++i) kb[i] = R(0);
+                if (on) digest_part<LA, LB, LC, LD, R, G>(B, K, I, sdeg, a, q, sub, jab, jcd, kb);
+                if (q == 0 && a.want_j) {
+                    const double f = 2.0 * (double)sdeg;
+#pragma unroll
+                    for (int l = 0; l < NC; ++l)
+#pragma unroll
+                        for (int s = 0; s < ND; ++s) {
+                            const R v = group_sum<R, G>(jcd[l * ND + s]);
+                            if (on && ((l * ND + s) % G) == sub)
+                                atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)v);
+                        }
+                }
+                if (a.want_k) {
+                    double* Kq = a.K + (size_t)q * n * n;
+                    const double f = (double)sdeg;
+                    int e = 0;
+#pragma unroll
+                    for (int m = 0; m < NA; ++m)
+#pragma unroll
+                        for (int l = 0; l < NC; ++l, ++e) {
+                            const R v = group_sum<R, G>(kb[m * NC + l]);
+                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)v);
+                        }
+#pragma unroll
+                    for (int m = 0; m < NA; ++m)
+#pragma unroll
+                        for (int s = 0; s < ND; ++s, ++e) {
+                            const R v = group_sum<R, G>(kb[NA * NC + m * ND + s]);
+                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)v);
+                        }
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+#pragma unroll
+                        for (int l = 0; l < NC; ++l, ++e) {
+                            const R v = group_sum<R, G>(kb[NA * NC + NA * ND + k * NC + l]);
+                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)v);
+                        }
+#pragma unroll
+                    for (int k = 0; k < NB; ++k)
+#pragma unroll
+                        for (int s = 0; s < ND; ++s, ++e) {
+                            const R v = group_sum<R, G>(kb[NA * NC + NA * ND + NB * NC + k * ND + s]);
+                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)v);
+                        }
+                }
+            }
         }
     }
     // warp reduction of the bra J' block, one writer per warp
