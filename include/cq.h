@@ -30,6 +30,8 @@
 #ifndef CQ_H
 #define CQ_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -112,6 +114,53 @@ typedef struct {
  * Im P contribute. */
 int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
                   const cq_fock_opts* opts, cq_fock_stats* stats, void* stream);
+
+/* cq_fock_build_noalloc: the same J/K build as cq_fock_build for callers
+ * that cannot have the library allocate device memory -- for example a host
+ * program that hands out all device memory from its own pool or fixed
+ * budget, or a loop that must not pay for cudaMalloc/cudaFree and the device
+ * synchronisation they may cause.  The paper has no counterpart; this is an
+ * interface of this library only.
+ *   - Allocates nothing: its scratch (scaled densities, J'/K' accumulators,
+ *     block maxima, counters) lives in one file-scope __device__ array of
+ *     16 MiB (16777216 bytes) that every GPU loading the library holds until
+ *     the library is unloaded.  cq_fock_noalloc_scratch_bytes(kind, nbf,
+ *     nshell) gives the bytes a build needs (about (2 nk + 1) nbf^2 doubles,
+ *     nk = 1 / 2 / 8 for REAL_SYM / COMPLEX_HERM / PAULI4); a basis that needs
+ *     more is rejected with CQ_ERR_INVALID_ARG before any work is enqueued.
+ *   - Arguments, layouts and results are those of cq_fock_build; there is no
+ *     stats output.  The basis must come from cq_basis_create (which does
+ *     allocate, once, ahead of time).
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  The first launch of the integral kernels in
+ *     a process may also make the driver enlarge its per-thread local-memory
+ *     reservation, so run one build before entering a region where no device
+ *     memory may be reserved.
+ *   - All calls share the one array, and it keeps the last call's contents
+ *     (the accumulators are cleared at the start of each call).  Calls whose
+ *     work overlaps on the GPU -- different streams, or different host
+ *     threads -- race on it and give wrong results: serialise them. */
+int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, double* J,
+                          void* K, const cq_fock_opts* opts, void* stream);
+size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell);
+
+/* Per-class profile of cq_fock_build (instrumentation, off by default).
+ * cq_fock_profile(b, 1) makes later builds record CUDA events around each
+ * angular-momentum-class kernel.  cq_fock_class_stats returns, for the last
+ * build, class qc (0..20, bra class X >= ket class Y, qc = X(X+1)/2 + Y with
+ * pair classes ss,ps,pp,ds,dp,dd = 0..5) and precision (fp32 0/1): kernel
+ * time in ms (0 if profiling was off), contracted and primitive quartets
+ * evaluated.  Synchronises the device. */
+int cq_fock_profile(cq_basis* b, int enable);
+int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
+                        unsigned long long* quartets, unsigned long long* prims);
+
+/* FMA throughput of the current device (FP64 if fp32 == 0, else FP32), in
+ * floating-point operations per second (an FMA counts 2), from independent
+ * FMA chains on every SM.  Measurement support for the roofline of the
+ * integral kernels; allocates and frees a small output buffer. */
+int cq_peak_fma(int fp32, int iters, double* flops_per_s, void* stream);
 
 /* Nuclear repulsion energy of the basis' nuclei (host result). */
 int cq_nuclear_repulsion(const cq_basis* b, double* E);

@@ -64,6 +64,9 @@ def lib():
                                           ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.POINTER(ctypes.c_ulonglong)]
         L.cq_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp]
+        L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
+        L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
         _lib = L
     return _lib
 

@@ -1,0 +1,148 @@
+// Allocation-free variant of cq_fock_build.
+//
+// Some callers cannot let a library call cudaMalloc on their behalf: hosts
+// that own every byte of device memory through their own allocator or a
+// fixed budget reserved up front, and latency-critical loops where an
+// allocation (and the device synchronisation cudaMalloc/cudaFree can imply)
+// is not acceptable once the loop runs.  cq_fock_build grows its per-build
+// scratch inside the basis handle on first use; this entry point instead
+// takes its scratch from one file-scope device array of fixed size, so it
+// never allocates.  The basis handle itself (created beforehand with
+// cq_basis_create) is unchanged.
+#include <cstring>
+#include <mutex>
+
+#include "cq_internal.h"
+#include "cq_jk.cuh"
+
+namespace cq {
+
+// kernels of the ordinary build (cq_fock.cu), reused unchanged
+__global__ void density_prep_kernel(int kind, int n, const double* __restrict__ P, const double* __restrict__ sc,
+                                    double* __restrict__ Dp);
+__global__ void dmax_kernel(int nsh, int n, int nk, const int* __restrict__ bfo, const double* __restrict__ Dp,
+                            float* __restrict__ Dmax);
+__global__ void finalize_kernel(int kind, int n, const double* __restrict__ sc, const double* __restrict__ Jp,
+                                const double* __restrict__ Kp, double* __restrict__ J, double* __restrict__ K,
+                                int want_j, int want_k);
+
+// Scratch of the allocation-free build: 16 MiB held by every device that
+// loads the library, for as long as the library stays loaded.
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_scratch_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+static std::mutex g_scratch_mu;
+
+static size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Device address of the scratch array on the current device (looked up once
+// per device; in host code the array's name is only a host-side stand-in).
+static int scratch_address(void** out)
+{
+    int dev = 0;
+    CQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("cq_fock_build_noalloc: device ordinal beyond the supported range");
+        return CQ_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return CQ_OK;
+}
+
+}  // namespace cq
+
+using namespace cq;
+
+extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
+{
+    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const size_t nn = (size_t)nbf * nbf;
+    return round256(nn * nk * sizeof(double)) * 2 + round256(nn * sizeof(double)) +
+           round256((size_t)nshell * nshell * sizeof(float)) + round256((4 + 4 * NQC) * sizeof(unsigned long long));
+}
+
+extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, double* J, void* K,
+                                     const cq_fock_opts* opts, void* stream)
+{
+    if (!b || !P) { set_error("cq_fock_build_noalloc: NULL basis or density"); return CQ_ERR_INVALID_ARG; }
+    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_PAULI4) {
+        set_error("cq_fock_build_noalloc: unknown density kind");
+        return CQ_ERR_INVALID_ARG;
+    }
+    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1};
+    if (opts) o = *opts;
+    if ((o.want_J && !J) || (o.want_K && !K)) {
+        set_error("cq_fock_build_noalloc: requested output pointer is NULL");
+        return CQ_ERR_INVALID_ARG;
+    }
+    if ((o.prec != CQ_PREC_FP64 && o.prec != CQ_PREC_MIXED) || !(o.schwarz_tol >= 0.0) ||
+        !(o.mixed_tol >= 0.0)) {
+        set_error("cq_fock_build_noalloc: bad options");
+        return CQ_ERR_INVALID_ARG;
+    }
+    const size_t need = cq_fock_noalloc_scratch_bytes(kind, b->nbf, b->nsh);
+    if (need > NOALLOC_SCRATCH_BYTES) {
+        set_error("cq_fock_build_noalloc: basis too large for the fixed 16 MiB scratch (needs " +
+                  std::to_string(need) + " bytes); use cq_fock_build");
+        return CQ_ERR_INVALID_ARG;
+    }
+    void* base = nullptr;
+    int rc = scratch_address(&base);
+    if (rc) return rc;
+    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const int n = b->nbf;
+    const size_t nn = (size_t)n * n;
+    unsigned char* p = (unsigned char*)base;
+    double* Dp = (double*)p;          p += round256(nn * nk * sizeof(double));
+    double* Kp = (double*)p;          p += round256(nn * nk * sizeof(double));
+    double* Jp = (double*)p;          p += round256(nn * sizeof(double));
+    float* Dmax = (float*)p;          p += round256((size_t)b->nsh * b->nsh * sizeof(float));
+    unsigned long long* cnt = (unsigned long long*)p;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)((nn + 255) / 256);
+    density_prep_kernel<<<nb, 256, 0, s>>>(kind, n, (const double*)P, b->d_scale, Dp);
+    dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, Dp, Dmax);
+    // the array keeps the previous call's contents: clear the accumulators
+    CQ_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(Kp, 0, nn * nk * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(cnt, 0, (4 + 4 * NQC) * sizeof(unsigned long long), s));
+    JKArgs a;
+    memset(&a, 0, sizeof a);
+    a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
+    a.Q = b->d_Qf; a.Dmax = Dmax; a.nsh = b->nsh;
+    a.tau = (float)o.schwarz_tol;
+    a.tau_mixed = (float)o.mixed_tol;
+    a.D = Dp; a.nk = nk; a.nbf = n;
+    a.want_j = o.want_J; a.want_k = o.want_K;
+    a.J = Jp; a.K = Kp;
+    a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
+    for (int qc = NQC - 1; qc >= 0; --qc) {
+        int X = 0;
+        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+        const int Y = qc - X * (X + 1) / 2;
+        a.tasks = b->d_tasks + b->task_off[qc];
+        a.ntasks = b->task_off[qc + 1] - b->task_off[qc];
+        if (a.ntasks == 0) continue;
+        a.ket_end = b->cls_off[Y + 1];
+        a.same_class = (X == Y);
+        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
+            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
+            a.counters = cnt + 4 + 4 * qc + 2 * pp;
+            JK_LAUNCH[qc](a, pp, s);
+        }
+    }
+    CQ_CUDA(cudaGetLastError());
+    finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, Jp, Kp, J, (double*)K, o.want_J, o.want_K);
+    CQ_CUDA(cudaGetLastError());
+    return CQ_OK;
+}
