@@ -162,6 +162,88 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
  * integral kernels; allocates and frees a small output buffer. */
 int cq_peak_fma(int fp32, int iters, double* flops_per_s, void* stream);
 
+/* One-electron matrices (device, nbf^2 f64 each): overlap S, kinetic T,
+ * nuclear attraction V (all nuclei of the basis) and dipole-moment integrals
+ * M_d = <m| r_d - origin_d |n> (3*nbf^2, d = x,y,z; no charge sign), the
+ * core Hamiltonian h = T + V of Eq. 2c_fock and the electric-dipole operator
+ * of the real-time perturbation (Sec. "Real-Time Electronic Dynamics").
+ * Any output may be NULL; origin: host double[3] or NULL for (0,0,0). */
+int cq_one_electron(cq_basis* b, double* S, double* T, double* V, double* M,
+                    const double* origin, void* stream);
+
+/* RHF direct SCF (Sec. "Self-Consistent Field Optimization": DIIS
+ * extrapolation of the Fock matrix; RS case of Eq. rh_1c), every Fock matrix
+ * from cq_fock_build.  Loewdin orthogonalisation S^{-1/2}, canonical when an
+ * overlap eigenvalue is below 1e-8.  Core-Hamiltonian guess unless D_in
+ * (device, nbf^2, per-spin density C_occ C_occ^T) is given.  Converged when
+ * |dE| < e_tol and rms(X^T (FDS - SDF) X) < d_tol after a full FP64 build.
+ *   prec = CQ_PREC_MIXED: FP32 for quartets with bound < mixed_tol until the
+ *   error rms drops below switch_tol, then full FP64 builds (final
+ *   iterations).  incremental = 1: Fock matrices built from the density
+ *   change, F_k = F_{k-1} + G[D_k - D_{k-1}], with a full rebuild every
+ *   full_every iterations and before convergence is declared.
+ * Outputs (device): D_out nbf^2 (required), F_out nbf^2 (may be NULL).
+ * Returns CQ_ERR_NOT_CONVERGED (stats filled) if max_iter is reached,
+ * CQ_ERR_NUMERIC on a non-finite energy.  Synchronises `stream` every
+ * iteration (convergence test on the host). */
+typedef struct {
+    double e_tol;        /* 1e-10 */
+    double d_tol;        /* 1e-8  */
+    int max_iter;        /* 128 */
+    int diis_size;       /* 1..8 */
+    int prec;            /* cq_prec */
+    double mixed_tol;    /* 1e-5 */
+    double schwarz_tol;  /* 1e-14 */
+    int incremental;     /* 0/1 */
+    int full_every;      /* 8 */
+    double switch_tol;   /* 1e-5 */
+} cq_scf_opts;
+typedef struct {
+    double energy;
+    int iterations, converged;
+    double last_rms;
+    unsigned long long quartets_fp64, quartets_fp32;  /* summed over iterations */
+    double ms;
+} cq_scf_stats;
+int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
+           double* D_out, double* F_out, cq_scf_stats* stats, void* stream);
+
+/* One closed-shell RT-TDHF step of the Liouville-von Neumann equation (Eq.
+ * lvn), in the orthonormal (Loewdin) basis:
+ *   MMUT  P_{k+1} = U P_{k-1} U^+,  U = exp(-2 i dt F(P_k, t_k));
+ *   EM2   (step 0, and every restart_every steps)
+ *         P_{k+1} = U P_k U^+,  U = exp(-i dt (F(P_k,t_k) + F(P_FE,t_{k+1}))/2),
+ *         P_FE = U_FE P_k U_FE^+,  U_FE = exp(-i dt F(P_k, t_k)).
+ * F(P, t) = h + 2J[P] - K[P] + E(t).M (Eq. td_pert; length gauge, electron
+ * charge -1; E(t) = field on [t_on, t_off), else 0), t_k = step*dt.  The
+ * exponentials are Taylor series with scaling and squaring (ZGEMMs).
+ * P_prev, P_cur: device nbf^2 c128 AO densities (per spin); on return
+ * P_prev <- P_cur and P_cur <- P_{k+1}.  P_prev may be NULL only for step 0.
+ * obs (host, may be NULL): observables of P_k (the density on entry), from
+ * the step's own Fock build: dipole = -2 Re Tr[M P] + sum_A Z_A R_A, Tr(PS),
+ * field-free energy Re Tr[(h + F0) P] + E_nuc (Eq. td_expectation). */
+typedef struct {
+    double dt;
+    double field[3];
+    double t_on, t_off;
+    int restart_every;   /* 50 */
+    int prec;            /* cq_prec */
+    double mixed_tol;
+    double schwarz_tol;
+} cq_rt_opts;
+typedef struct {
+    double dipole[3];
+    double trPS;
+    double energy;
+    int em2;             /* 1 if this step was an EM2 step */
+} cq_rt_obs;
+int cq_rt_step(cq_basis* b, const cq_rt_opts* opts, int step, void* P_prev,
+               void* P_cur, cq_rt_obs* obs, void* stream);
+
+/* Number of orthonormal functions (columns of X) and dropped overlap
+ * eigenvectors; computes the one-electron data on first use. */
+int cq_dense_info(cq_basis* b, int* northo, int* ndropped, void* stream);
+
 /* Nuclear repulsion energy of the basis' nuclei (host result). */
 int cq_nuclear_repulsion(const cq_basis* b, double* E);
 

@@ -36,6 +36,30 @@ class FockStats(ctypes.Structure):
                 ("ms", ctypes.c_double)]
 
 
+class SCFOpts(ctypes.Structure):
+    _fields_ = [("e_tol", ctypes.c_double), ("d_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
+                ("diis_size", ctypes.c_int), ("prec", ctypes.c_int), ("mixed_tol", ctypes.c_double),
+                ("schwarz_tol", ctypes.c_double), ("incremental", ctypes.c_int), ("full_every", ctypes.c_int),
+                ("switch_tol", ctypes.c_double)]
+
+
+class SCFStats(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("last_rms", ctypes.c_double), ("quartets_fp64", ctypes.c_ulonglong),
+                ("quartets_fp32", ctypes.c_ulonglong), ("ms", ctypes.c_double)]
+
+
+class RTOpts(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("field", ctypes.c_double * 3), ("t_on", ctypes.c_double),
+                ("t_off", ctypes.c_double), ("restart_every", ctypes.c_int), ("prec", ctypes.c_int),
+                ("mixed_tol", ctypes.c_double), ("schwarz_tol", ctypes.c_double)]
+
+
+class RTObs(ctypes.Structure):
+    _fields_ = [("dipole", ctypes.c_double * 3), ("trPS", ctypes.c_double), ("energy", ctypes.c_double),
+                ("em2", ctypes.c_int)]
+
+
 def build():
     from . import buildlib as _b
     return _b.build()
@@ -64,6 +88,10 @@ def lib():
                                           ctypes.POINTER(ctypes.c_ulonglong),
                                           ctypes.POINTER(ctypes.c_ulonglong)]
         L.cq_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp]
+        L.cq_one_electron.argtypes = [vp, vp, vp, vp, vp, dp, vp]
+        L.cq_scf.argtypes = [vp, ctypes.c_int, ctypes.POINTER(SCFOpts), vp, vp, vp, ctypes.POINTER(SCFStats), vp]
+        L.cq_rt_step.argtypes = [vp, ctypes.POINTER(RTOpts), ctypes.c_int, vp, vp, ctypes.POINTER(RTObs), vp]
+        L.cq_dense_info.argtypes = [vp, ip, ip, vp]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
         L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
@@ -196,3 +224,54 @@ class Basis:
                     out[key] = {"qc": qc, "fp32": p, "ms": ms.value, "quartets": nq.value,
                                 "prims": npq.value}
         return out
+
+    def one_electron(self, origin=(0.0, 0.0, 0.0), stream=None):
+        """S, T, V (nbf x nbf) and dipole moment integrals M (3, nbf, nbf)."""
+        import torch
+        n = self.nbf
+        S, T, V = (torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(3))
+        M = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+        o = (ctypes.c_double * 3)(*origin)
+        check(lib().cq_one_electron(self.h, _ptr(S), _ptr(T), _ptr(V), _ptr(M), o, _stream_ptr(stream)),
+              "cq_one_electron")
+        return S, T, V, M
+
+    def scf(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
+            mixed_tol=1e-5, schwarz_tol=1e-14, incremental=False, full_every=8, switch_tol=1e-5,
+            D0=None, stream=None, raise_on_fail=True):
+        """RHF SCF; returns (D, F, stats dict)."""
+        import torch
+        n = self.nbf
+        D = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        F = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, int(incremental),
+                    full_every, switch_tol)
+        st = SCFStats()
+        rc = lib().cq_scf(self.h, int(nocc), ctypes.byref(o), _ptr(D0) if D0 is not None else None,
+                          _ptr(D), _ptr(F), ctypes.byref(st), _stream_ptr(stream))
+        if raise_on_fail:
+            check(rc, "cq_scf")
+        stats = {"energy": st.energy, "iterations": st.iterations, "converged": bool(st.converged),
+                 "last_rms": st.last_rms, "quartets_fp64": st.quartets_fp64,
+                 "quartets_fp32": st.quartets_fp32, "ms": st.ms, "rc": rc}
+        return D, F, stats
+
+    def rt_step(self, step, P_prev, P_cur, dt=0.05, field=(0.0, 0.0, 0.0), t_on=0.0, t_off=0.0,
+                restart_every=50, prec=CQ_PREC_FP64, mixed_tol=1e-5, schwarz_tol=1e-14, obs=True,
+                stream=None):
+        """One MMUT/EM2 step; P_prev, P_cur complex128 (nbf, nbf) CUDA tensors updated in
+        place.  Returns the observables of the density on entry (dict) or None."""
+        o = RTOpts(dt, (ctypes.c_double * 3)(*field), t_on, t_off, restart_every, prec, mixed_tol,
+                   schwarz_tol)
+        ob = RTObs()
+        check(lib().cq_rt_step(self.h, ctypes.byref(o), int(step), _ptr(P_prev), _ptr(P_cur),
+                               ctypes.byref(ob) if obs else None, _stream_ptr(stream)), "cq_rt_step")
+        if not obs:
+            return None
+        return {"dipole": list(ob.dipole), "trPS": ob.trPS, "energy": ob.energy, "em2": bool(ob.em2)}
+
+    def dense_info(self, stream=None):
+        m, d = ctypes.c_int(), ctypes.c_int()
+        check(lib().cq_dense_info(self.h, ctypes.byref(m), ctypes.byref(d), _stream_ptr(stream)),
+              "cq_dense_info")
+        return m.value, d.value

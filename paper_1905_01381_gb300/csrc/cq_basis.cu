@@ -141,6 +141,7 @@ extern "C" const char* cq_last_error(void) { return cq::g_err.c_str(); }
 static void free_basis(cq_basis* b)
 {
     if (!b) return;
+    dense_free(b);
     void* ptrs[] = {b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
                     b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
                     b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,

@@ -91,4 +91,26 @@ struct cq_basis {
     cudaEvent_t pev[cq::NQC][2][2] = {};
     bool pev_used[cq::NQC][2] = {};
     unsigned long long pcnt[cq::NQC][2][2] = {};
+    // dense drivers (SCF, RT): library handles and cached one-electron data
+    void* blas = nullptr;          // cublasHandle_t
+    void* solver = nullptr;        // cusolverDnHandle_t
+    int dense_ready = 0;
+    int northo = 0;                // columns of the orthogonaliser X (n x northo)
+    int ndropped = 0;
+    double enuc = 0.0;
+    double* d_S = nullptr;
+    double* d_H = nullptr;         // core Hamiltonian
+    double* d_M = nullptr;         // 3 dipole matrices
+    double* d_X = nullptr;         // orthogonaliser, n x northo
+    double* d_Xinv = nullptr;      // X^T S, northo x n
+    double* d_w = nullptr;         // eigenvalue workspace
+    double* d_work = nullptr;      // cusolver workspace
+    int lwork = 0;
+    int* d_info = nullptr;
+    std::vector<void*> dense_bufs; // other driver scratch, freed with the basis
+    void* rt = nullptr;            // RT-TDHF buffers (cq_drivers.cu)
 };
+
+namespace cq {
+void dense_free(cq_basis* b);
+}

@@ -1,0 +1,107 @@
+"""GPU one-electron integrals, RHF SCF and RT-TDHF steps against the oracle
+(FP64 targets: 1e-10 Eh in energy; one-electron matrices to 1e-12)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cq():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1905_01381_gb300 as cq
+    cq.build()
+    return cq
+
+
+@pytest.fixture(scope="module")
+def dr():
+    import oracle
+    oracle.build()
+    from oracle import drivers
+    return drivers
+
+
+def _mixed_case():
+    mol = synth.cluster(4, 91, counts={8: 1, 7: 1, 1: 2})
+    return mol, synth.basis_spd(mol, 92, max_depth=3)
+
+
+def test_one_electron(cq):
+    import oracle
+    mol, bas = _mixed_case()
+    b = cq.Basis(mol, bas)
+    ob = oracle.OBasis(mol, bas)
+    S, T, V, M = (x.cpu().numpy() for x in b.one_electron(origin=(0.2, -0.1, 0.3)))
+    assert np.abs(S - oracle.overlap(ob)).max() < 1e-12
+    assert np.abs(T - oracle.kinetic(ob)).max() < 1e-11
+    assert np.abs(V - oracle.nuclear(ob)).max() < 1e-10
+    assert np.abs(M - oracle.dipole(ob, origin=(0.2, -0.1, 0.3))).max() < 1e-12
+    assert abs(b.nuclear_repulsion() - oracle.nuclear_repulsion(mol)) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["triatomic", "mixed"])
+def test_rhf_energy_matches_oracle(cq, dr, case):
+    mol, bas = synth.workload_triatomic() if case == "triatomic" else _mixed_case()
+    nocc = mol.n_electrons(mol.closed_shell_charge()) // 2
+    b = cq.Basis(mol, bas)
+    D, F, st = b.scf(nocc)
+    ref = dr.rhf(dr.System(mol, bas), nocc)
+    assert st["converged"] and ref.converged
+    assert abs(st["energy"] - ref.energy) < 1e-10, (st["energy"], ref.energy)
+    Dg = D.cpu().numpy()
+    assert np.abs(Dg - ref.D).max() < 1e-6
+    S = b.one_electron()[0].cpu().numpy()
+    assert abs(np.trace(Dg @ S) - nocc) < 1e-10
+
+
+def test_rhf_mixed_incremental_same_energy(cq):
+    mol, bas = _mixed_case()
+    nocc = mol.n_electrons(mol.closed_shell_charge()) // 2
+    b = cq.Basis(mol, bas)
+    _, _, st64 = b.scf(nocc)
+    _, _, stm = b.scf(nocc, prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, incremental=True)
+    assert stm["converged"]
+    assert stm["quartets_fp32"] > 0
+    assert abs(stm["energy"] - st64["energy"]) < 1e-10
+
+
+def test_rt_matches_oracle_step_by_step(cq, dr):
+    import torch
+    mol, bas = synth.workload_triatomic()
+    b = cq.Basis(mol, bas)
+    D, _, _ = b.scf(5)
+    Pc = D.to(torch.complex128).clone()
+    Pp = Pc.clone()
+    s = dr.System(mol, bas)
+    r = dr.rhf(s, 5)
+    field = dict(field=(0.0, 0.0, 1e-3), t_on=0.0, t_off=0.05)
+    rt = dr.RT(s, D.cpu().numpy(), 0.05, dr.Field((0.0, 0.0, 1e-3), 0.0, 0.05), restart=5)
+    gobs, oobs = [], []
+    for k in range(12):
+        gobs.append(b.rt_step(k, Pp, Pc, dt=0.05, restart_every=5, **field))
+        oobs.append(rt.step())
+    for k in range(11):
+        g, o = gobs[k + 1], oobs[k]
+        assert np.abs(np.array(g["dipole"]) - o[0]).max() < 1e-9, k
+        assert abs(g["trPS"] - o[1]) < 1e-10
+        assert abs(g["energy"] - o[2]) < 1e-10
+    assert gobs[0]["em2"] and gobs[5]["em2"] and not gobs[1]["em2"]
+    assert abs(gobs[0]["energy"] - r.energy) < 1e-10
+
+
+def test_rt_zero_field_stationary(cq):
+    import torch
+    mol, bas = synth.workload_triatomic()
+    b = cq.Basis(mol, bas)
+    D, _, _ = b.scf(5, e_tol=1e-12, d_tol=1e-11, max_iter=200)
+    Pc = D.to(torch.complex128).clone()
+    Pp = Pc.clone()
+    P0 = Pc.clone()
+    for k in range(6):
+        b.rt_step(k, Pp, Pc, dt=0.05)
+    assert (Pc - P0).abs().max().item() < 1e-8
