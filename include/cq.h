@@ -156,6 +156,15 @@ int cq_fock_profile(cq_basis* b, int enable);
 int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
                         unsigned long long* quartets, unsigned long long* prims);
 
+/* Kernel variant used for one angular-momentum class (qc as for
+ * cq_fock_class_stats) and precision: 0 = lane-group kernel (lanes of a warp
+ * split one quartet's primitive quartets, generated straight-line
+ * recurrences), 1 = warp-cooperative kernel (one warp per quartet walking
+ * generated recurrence tables through shared memory).  Both give the same
+ * J/K to rounding; the choice only changes speed (set by the autotuner). */
+int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
+int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
+
 /* FMA throughput of the current device (FP64 if fp32 == 0, else FP32), in
  * floating-point operations per second (an FMA counts 2), from independent
  * FMA chains on every SM.  Measurement support for the roofline of the

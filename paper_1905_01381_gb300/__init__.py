@@ -92,6 +92,8 @@ def lib():
         L.cq_scf.argtypes = [vp, ctypes.c_int, ctypes.POINTER(SCFOpts), vp, vp, vp, ctypes.POINTER(SCFStats), vp]
         L.cq_rt_step.argtypes = [vp, ctypes.POINTER(RTOpts), ctypes.c_int, vp, vp, ctypes.POINTER(RTObs), vp]
         L.cq_dense_info.argtypes = [vp, ip, ip, vp]
+        L.cq_fock_set_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+        L.cq_fock_get_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
         L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
@@ -275,3 +277,11 @@ class Basis:
         check(lib().cq_dense_info(self.h, ctypes.byref(m), ctypes.byref(d), _stream_ptr(stream)),
               "cq_dense_info")
         return m.value, d.value
+
+    def set_variant(self, qc, fp32, variant):
+        check(lib().cq_fock_set_variant(self.h, int(qc), int(fp32), int(variant)), "cq_fock_set_variant")
+
+    def get_variant(self, qc, fp32):
+        v = ctypes.c_int()
+        check(lib().cq_fock_get_variant(self.h, int(qc), int(fp32), ctypes.byref(v)), "cq_fock_get_variant")
+        return v.value

@@ -19,7 +19,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "--expt-relaxed-constexpr", "-Xptxas=-warn-spills", "-I", CSRC, "-I", GEN,
                   "-I", os.path.join(os.path.dirname(HERE), "include")]
-HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu", "cq_peaks.cu", "cq_noalloc.cu", "cq_oneint.cu", "cq_drivers.cu"]
+HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu", "cq_peaks.cu", "cq_noalloc.cu", "cq_oneint.cu", "cq_drivers.cu",
+                "cq_coop.cu"]
 LIBS = ["-lcublas", "-lcusolver"]
 
 PCS = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]
@@ -41,8 +42,13 @@ def qclasses():
 def gen_sources():
     sys.path.insert(0, CSRC)
     import gen_eri  # noqa: E402
-    sys.path.pop(0)
     stats = gen_eri.main(GEN)
+    import gen_coop  # noqa: E402
+    code, _ = gen_coop.emit(GEN, gen_eri.classes())
+    path = os.path.join(GEN, "coop_tables.cuh")
+    if not os.path.exists(path) or open(path).read() != code:
+        with open(path, "w") as fh:
+            fh.write(code)
     tus = []
 
     def write(path, lines):
@@ -96,6 +102,7 @@ def gen_sources():
              ", ".join(f"launch_schwarz_{X[0]}{X[1]}" for X in PCS) + "};")
     d.append("}  // namespace cq")
     write(os.path.join(GEN, "cq_dispatch.cu"), d)
+    sys.path.remove(CSRC)
     return tus, stats
 
 
@@ -111,6 +118,8 @@ def _deps_mtime():
 def _compile(src, verbose=False):
     obj = os.path.join(OBJ, os.path.basename(src).replace(".cu", ".o"))
     dm = max(_deps_mtime(), os.path.getmtime(src))
+    if os.path.basename(src) == "cq_coop.cu":
+        dm = max(dm, os.path.getmtime(os.path.join(GEN, "coop_tables.cuh")))
     if os.path.exists(obj) and os.path.getmtime(obj) >= dm:
         return obj, ""
     cmd = ["nvcc", "-c", src, "-o", obj + ".tmp"] + NVFLAGS

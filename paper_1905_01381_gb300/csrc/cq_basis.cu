@@ -12,6 +12,10 @@ namespace cq {
 
 const int PC_L[NPC][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
 
+// warp-cooperative kernel for the classes with the largest recurrences:
+// (dp|pp) (dp|ds) (dp|dp) (dd|ps) (dd|pp) (dd|ds) (dd|dp) (dd|dd)
+const int DEFAULT_VARIANT[NQC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 1, 1, 1, 1, 1};
+
 static thread_local std::string g_err;
 
 void set_error(const std::string& msg) { g_err = msg; }
@@ -171,6 +175,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
                        const double* coefs, cq_basis* b)
 {
     CQ_CUDA(cudaGetDevice(&b->device));
+    for (int q = 0; q < NQC; ++q) b->variant[q][0] = b->variant[q][1] = DEFAULT_VARIANT[q];
     b->natom = natom;
     b->nsh = nshell;
     b->xyz.assign(xyz, xyz + 3 * natom);
@@ -226,23 +231,31 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     for (auto& h : b->pairs) { h.poff = q; q += h.nprim; }
     b->nprim_pairs = q;
 
-    // ---- warp tasks per quartet class: (bra, first ket candidate), costliest first
+    // ---- warp tasks per quartet class: (bra, ket candidates [j0, j1)),
+    // costliest first.  The candidate range per task shrinks for classes
+    // with few quartets so that every class offers enough warps to fill the
+    // GPU (about 32 per SM).
     b->task_off.assign(NQC + 1, 0);
-    std::vector<int2> tasks;
+    std::vector<int4> tasks;
     for (int X = 0, qc = 0; X < NPC; ++X)
         for (int Y = 0; Y <= X; ++Y, ++qc) {
             b->task_off[qc] = (int)tasks.size();
-            std::vector<std::pair<double, int2>> tv;
+            const long nbra = b->cls_off[X + 1] - b->cls_off[X], nket = b->cls_off[Y + 1] - b->cls_off[Y];
+            const long cand = (X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket;
+            int range = (int)std::min<long>(JK_RANGE, std::max<long>(4, cand / (152 * 32)));
+            range = std::max(4, range & ~3);
+            std::vector<std::pair<double, int4>> tv;
             for (int i = b->cls_off[X]; i < b->cls_off[X + 1]; ++i) {
                 const int jb = b->cls_off[Y], je = (X == Y) ? i + 1 : b->cls_off[Y + 1];
-                for (int j0 = jb; j0 < je; j0 += JK_RANGE) {
+                for (int j0 = jb; j0 < je; j0 += range) {
+                    const int j1 = std::min(je, j0 + range);
                     double cost = 0.0;
-                    for (int j = j0; j < std::min(je, j0 + JK_RANGE); ++j) cost += b->pairs[j].nprim;
-                    tv.push_back({cost * b->pairs[i].nprim, make_int2(i, j0)});
+                    for (int j = j0; j < j1; ++j) cost += b->pairs[j].nprim;
+                    tv.push_back({cost * b->pairs[i].nprim, make_int4(i, j0, j1, 0)});
                 }
             }
             std::stable_sort(tv.begin(), tv.end(),
-                             [](const std::pair<double, int2>& x, const std::pair<double, int2>& y) {
+                             [](const std::pair<double, int4>& x, const std::pair<double, int4>& y) {
                                  return x.first > y.first;
                              });
             for (auto& t : tv) tasks.push_back(t.second);

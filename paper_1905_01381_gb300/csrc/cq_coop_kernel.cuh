@@ -1,0 +1,272 @@
+// Kernel of the warp-cooperative path; included after coop_tables.cuh,
+// which defines COOP_CLASSES_D.
+#pragma once
+#include "cq_coop.cuh"
+
+namespace cq {
+
+template <typename R>
+__device__ __forceinline__ void boys_rt_any(int L, R T, R* F, const R* tab)
+{
+    switch (L) {
+        case 0: boys<0>(T, F, tab); break;
+        case 1: boys<1>(T, F, tab); break;
+        case 2: boys<2>(T, F, tab); break;
+        case 3: boys<3>(T, F, tab); break;
+        case 4: boys<4>(T, F, tab); break;
+        case 5: boys<5>(T, F, tab); break;
+        case 6: boys<6>(T, F, tab); break;
+        case 7: boys<7>(T, F, tab); break;
+        default: boys<8>(T, F, tab); break;
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
+{
+    const CoopClass C = COOP_CLASSES_D[qc];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* wbase = smem_raw + (size_t)wib * coop_warp_bytes<R>(nslots_max);
+    R* coef = (R*)wbase;                                   // [32][NCOEF]
+    R* Sb = coef + 32 * COOP_NCOEF;                        // [32][LTOT_MAX+1]
+    R* V = Sb + 32 * (LTOT_MAX + 1);                       // [nslots]
+    R* Db = V + nslots_max;                                // 6 density blocks of <= 36
+    R* hc = Db + 6 * 36;                                   // AB, CD
+    int* qw = (int*)(hc + 8);                              // queue of 64
+
+    const int w = blockIdx.x * COOP_WARPS + wib;
+    if (w >= a.ntasks) return;
+    const int4 t = a.tasks[w];
+    const int ib = t.x;
+    const int jend = t.z;
+    const PairHdr B = a.pairs[ib];
+    const float Qb = __ldg(a.Q + ib);
+    const float* Dm = a.Dmax;
+    const int ns = a.nsh;
+    const float dab_max = __ldg(Dm + B.a * ns + B.b);
+    const int NA = ncart(C.la), NB = ncart(C.lb), NC = ncart(C.lc), ND = ncart(C.ld);
+    const R* boys_tab;
+    if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
+    const int n = a.nbf;
+    unsigned long long nq = 0, np = 0;
+    int qn = 0, c0 = t.y;
+    while (true) {
+        while (qn < 1 && c0 < jend) {
+            const int j = c0 + lane;
+            bool sel = false;
+            if (j < jend) {
+                const int kc = __ldg(&a.pairs[j].a), kd = __ldg(&a.pairs[j].b);
+                float m = fmaxf(dab_max, __ldg(Dm + kc * ns + kd));
+                m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + kc), __ldg(Dm + B.a * ns + kd)));
+                m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + kc), __ldg(Dm + B.b * ns + kd)));
+                const float bound = Qb * __ldg(a.Q + j) * m;
+                sel = bound >= a.tau;
+                if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
+                else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, sel);
+            if (sel) qw[qn + __popc(msk & ((1u << lane) - 1u))] = j;
+            qn += __popc(msk);
+            c0 += 32;
+            __syncwarp();
+        }
+        if (qn == 0) break;
+        const int j = qw[0];
+        const int mv = lane + 1 < qn ? qw[lane + 1] : 0;
+        __syncwarp();
+        if (lane + 1 < qn) qw[lane] = mv;
+        __syncwarp();
+        qn -= 1;
+        const PairHdr K = a.pairs[j];
+
+        // ---- primitive quartets: coefficients, VRR, accumulation
+        R acc[COOP_MAXACC];
+#pragma unroll
+        for (int k = 0; k < COOP_MAXACC; ++k) acc[k] = R(0);
+        const int nkp = K.nprim, tot = B.nprim * K.nprim;
+        for (int base = 0; base < tot; base += 32) {
+            const int cnt = min(32, tot - base);
+            if (lane < cnt) {
+                const int pq = base + lane;
+                const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
+                PrimPairT<R> bp, kp;
+                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                const R s = bp.zeta + kp.zeta;
+                const R rs = rsqrt_r(s);
+                const R is = rs * rs;
+                const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
+                const R roz = kp.zeta * is, roe = bp.zeta * is;
+                const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
+                R F[LTOT_MAX + 1];
+                boys_rt_any<R>(C.L, T, F, boys_tab);
+                const R pref = bp.K * kp.K * rs;
+                R* cf = coef + lane * COOP_NCOEF;
+                cf[0] = bp.PA[0]; cf[1] = bp.PA[1]; cf[2] = bp.PA[2];
+                cf[3] = kp.PA[0]; cf[4] = kp.PA[1]; cf[5] = kp.PA[2];
+                cf[6] = -roz * PQx; cf[7] = -roz * PQy; cf[8] = -roz * PQz;
+                cf[9] = roe * PQx; cf[10] = roe * PQy; cf[11] = roe * PQz;
+                cf[12] = roz; cf[13] = roe;
+                const R o2ze = R(0.5) * is;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cf[14 + k] = R(k + 1) * bp.oo2z;
+                    cf[18 + k] = R(k + 1) * kp.oo2z;
+                    cf[22 + k] = R(k + 1) * o2ze;
+                }
+                R* sb = Sb + lane * (LTOT_MAX + 1);
+                for (int m = 0; m <= C.L; ++m) sb[m] = pref * F[m];
+            }
+            __syncwarp();
+            for (int q = 0; q < cnt; ++q) {
+                if (lane <= C.L) V[lane] = Sb[q * (LTOT_MAX + 1) + lane];
+                __syncwarp();
+                const R* cf = coef + q * COOP_NCOEF;
+                for (int g = 0; g < C.nvg; ++g) {
+                    const int4 G = __ldg(C.vgrp + g);
+                    if (lane < G.y) {
+                        const int4 d = __ldg(C.vdesc + G.z + lane);
+                        const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
+                        const int cw = d.w;
+                        R v = cf[cw & 63] * V[x0];
+                        v = fma(cf[(cw >> 6) & 63], V[x1], v);
+                        if (G.x == 1 || G.x == 3) {
+                            const int x2 = d.y & 0xffff, x3 = (unsigned)d.y >> 16;
+                            v = fma(cf[(cw >> 12) & 63], fma(-cf[(cw >> 18) & 63], V[x3], V[x2]), v);
+                        }
+                        if (G.x >= 2) {
+                            const int x4 = d.z & 0xffff;
+                            v = fma(cf[(cw >> 24) & 63], V[x4], v);
+                        }
+                        V[(unsigned)d.z >> 16] = v;
+                    }
+                    if (G.w) __syncwarp();
+                }
+#pragma unroll
+                for (int k = 0; k < COOP_MAXACC; ++k) {
+                    const int tt = lane + 32 * k;
+                    if (tt < C.nacc) acc[k] += V[__ldg(C.tgt + tt)];
+                }
+                __syncwarp();
+            }
+            if (lane == 0) { nq += (base == 0); np += cnt; }
+        }
+
+        // ---- horizontal recurrence on the contracted block
+#pragma unroll
+        for (int k = 0; k < COOP_MAXACC; ++k) {
+            const int tt = lane + 32 * k;
+            if (tt < C.nacc) V[C.N + tt] = acc[k];
+        }
+        if (lane < 3) { hc[lane] = (R)B.AB[lane]; hc[3 + lane] = (R)K.AB[lane]; }
+        __syncwarp();
+        for (int g = 0; g < C.nhg; ++g) {
+            const int4 G = __ldg(C.hgrp + g);
+            if (lane < G.y) {
+                const int4 d = __ldg(C.hdesc + G.z + lane);
+                const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
+                const R v = (G.x == 0) ? fma(hc[d.w & 63], V[x1], V[x0]) : V[x0];
+                V[(unsigned)d.z >> 16] = v;
+            }
+            if (G.w) __syncwarp();
+        }
+        __syncwarp();
+
+        // ---- output-stationary digestion
+        R sdeg = R(1);
+        if (B.a == B.b) sdeg *= R(0.5);
+        if (K.a == K.b) sdeg *= R(0.5);
+        if (j == ib) sdeg *= R(0.5);
+        const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+        const int nJ = (a.want_j ? NA * NB + NC * ND : 0);
+        const int nK = (a.want_k ? NA * NC + NA * ND + NB * NC + NB * ND : 0);
+        for (int q = 0; q < a.nk; ++q) {
+            if (q > 0 && !a.want_k) break;
+            const double* Dq = a.D + (size_t)q * n * n;
+            double* Kq = a.K + (size_t)q * n * n;
+            // density blocks: ab, cd, bd, bc, ad, ac (each <= 36)
+            for (int e = lane; e < 216; e += 32) {
+                const int blk = e / 36, r = e - blk * 36;
+                int rr = 0, cc = 0, nr = 0, ncol = 0;
+                switch (blk) {
+                    case 0: nr = NA; ncol = NB; rr = fa; cc = fb; break;
+                    case 1: nr = NC; ncol = ND; rr = fc; cc = fd; break;
+                    case 2: nr = NB; ncol = ND; rr = fb; cc = fd; break;
+                    case 3: nr = NB; ncol = NC; rr = fb; cc = fc; break;
+                    case 4: nr = NA; ncol = ND; rr = fa; cc = fd; break;
+                    default: nr = NA; ncol = NC; rr = fa; cc = fc; break;
+                }
+                if (r < nr * ncol) Db[e] = ldR<R>(Dq + (size_t)(rr + r / ncol) * n + cc + r % ncol);
+            }
+            __syncwarp();
+            const int nout = (q == 0 ? nJ : 0) + nK;
+            for (int o = lane; o < nout; o += 32) {
+                int kind = 0, oo = o;
+                if (q != 0) kind = 2;
+                if (q == 0 && oo >= nJ) { kind = 2; oo -= nJ; }
+                R sum = R(0);
+                double* dst;
+                double f;
+                if (kind == 0 && oo < NA * NB) {            // J'_ab
+                    const int m = oo / NB, k = oo % NB;
+                    for (int ls = 0; ls < NC * ND; ++ls) sum = fma(V[(m * NB + k) * NC * ND + ls], Db[36 + ls], sum);
+                    dst = a.J + (size_t)(fa + m) * n + fb + k;
+                    f = 2.0 * (double)sdeg;
+                } else if (kind == 0) {                       // J'_cd
+                    oo -= NA * NB;
+                    const int l = oo / ND, s = oo % ND;
+                    for (int mk = 0; mk < NA * NB; ++mk) sum = fma(V[mk * NC * ND + l * ND + s], Db[mk], sum);
+                    dst = a.J + (size_t)(fc + l) * n + fd + s;
+                    f = 2.0 * (double)sdeg;
+                } else if (oo < NA * NC) {                    // K'_ac += (ab|cd) D_bd
+                    const int m = oo / NC, l = oo % NC;
+                    for (int k = 0; k < NB; ++k)
+                        for (int s = 0; s < ND; ++s)
+                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[72 + k * ND + s], sum);
+                    dst = Kq + (size_t)(fa + m) * n + fc + l;
+                    f = (double)sdeg;
+                } else if (oo < NA * NC + NA * ND) {          // K'_ad += (ab|cd) D_bc
+                    oo -= NA * NC;
+                    const int m = oo / ND, s = oo % ND;
+                    for (int k = 0; k < NB; ++k)
+                        for (int l = 0; l < NC; ++l)
+                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[108 + k * NC + l], sum);
+                    dst = Kq + (size_t)(fa + m) * n + fd + s;
+                    f = (double)sdeg;
+                } else if (oo < NA * NC + NA * ND + NB * NC) {  // K'_bc += (ab|cd) D_ad
+                    oo -= NA * NC + NA * ND;
+                    const int k = oo / NC, l = oo % NC;
+                    for (int m = 0; m < NA; ++m)
+                        for (int s = 0; s < ND; ++s)
+                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[144 + m * ND + s], sum);
+                    dst = Kq + (size_t)(fb + k) * n + fc + l;
+                    f = (double)sdeg;
+                } else {                                       // K'_bd += (ab|cd) D_ac
+                    oo -= NA * NC + NA * ND + NB * NC;
+                    const int k = oo / ND, s = oo % ND;
+                    for (int m = 0; m < NA; ++m)
+                        for (int l = 0; l < NC; ++l)
+                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[180 + m * NC + l], sum);
+                    dst = Kq + (size_t)(fb + k) * n + fd + s;
+                    f = (double)sdeg;
+                }
+                atomicAdd(dst, f * (double)sum);
+            }
+            __syncwarp();
+        }
+    }
+    if (a.counters) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            nq += __shfl_xor_sync(0xffffffffu, nq, o);
+            np += __shfl_xor_sync(0xffffffffu, np, o);
+        }
+        if (lane == 0 && nq) {
+            atomicAdd(a.counters + 0, nq);
+            atomicAdd(a.counters + 1, np);
+        }
+    }
+}
+
+}  // namespace cq

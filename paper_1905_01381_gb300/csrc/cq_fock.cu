@@ -113,9 +113,35 @@ int ensure_scratch(cq_basis* b, int nk)
     return CQ_OK;
 }
 
+void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s)
+{
+    if (b->variant[qc][fp32] == VARIANT_COOP) launch_coop(a, qc, fp32, s);
+    else JK_LAUNCH[qc](a, fp32, s);
+}
+
 }  // namespace cq
 
 using namespace cq;
+
+extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
+{
+    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1 || variant < 0 || variant > 1) {
+        set_error("cq_fock_set_variant: bad argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    b->variant[qc][fp32] = variant;
+    return CQ_OK;
+}
+
+extern "C" int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant)
+{
+    if (!b || !variant || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1) {
+        set_error("cq_fock_get_variant: bad argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    *variant = b->variant[qc][fp32];
+    return CQ_OK;
+}
 
 extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
                              const cq_fock_opts* opts, cq_fock_stats* stats, void* stream)
@@ -183,7 +209,7 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
                     if (!b->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&b->pev[qc][pp][e]));
                 CQ_CUDA(cudaEventRecord(b->pev[qc][pp][0], s));
             }
-            JK_LAUNCH[qc](a, pp, s);
+            launch_jk_class(b, a, qc, pp, s);
             if (b->profile) {
                 CQ_CUDA(cudaEventRecord(b->pev[qc][pp][1], s));
                 b->pev_used[qc][pp] = true;

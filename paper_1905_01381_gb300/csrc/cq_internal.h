@@ -22,6 +22,12 @@ using LaunchJK = void (*)(const JKArgs&, int fp32, cudaStream_t);
 using LaunchSchwarz = void (*)(const JKArgs&, int, int, float*, double*, cudaStream_t);
 extern const LaunchJK JK_LAUNCH[NQC];          // index: X*(X+1)/2 + Y
 extern const LaunchSchwarz SCHWARZ_LAUNCH[NPC];
+void launch_coop(const JKArgs& a, int qc, int fp32, cudaStream_t s);
+size_t coop_smem_bytes(int qc, int fp32);
+
+// kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative
+constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1;
+extern const int DEFAULT_VARIANT[NQC];
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
@@ -65,7 +71,7 @@ struct cq_basis {
     cq::PairHdr* d_pairs = nullptr;
     cq::PrimPair* d_prims = nullptr;
     cq::PrimPairF* d_primsf = nullptr;
-    int2* d_tasks = nullptr;
+    int4* d_tasks = nullptr;
     float* d_Qf = nullptr;
     double* d_Qd = nullptr;
     double* d_scale = nullptr;     // per-function Cartesian component factor
@@ -109,7 +115,12 @@ struct cq_basis {
     int* d_info = nullptr;
     std::vector<void*> dense_bufs; // other driver scratch, freed with the basis
     void* rt = nullptr;            // RT-TDHF buffers (cq_drivers.cu)
+    int variant[cq::NQC][2] = {};  // kernel variant per class and precision
 };
+
+namespace cq {
+void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s);
+}
 
 namespace cq {
 void dense_free(cq_basis* b);

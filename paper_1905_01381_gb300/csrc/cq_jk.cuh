@@ -7,13 +7,13 @@
 namespace cq {
 
 constexpr int JK_THREADS = 128;   // 4 warps per CTA
-constexpr int JK_RANGE = 64;      // ket candidates per warp task
+constexpr int JK_RANGE = 64;      // largest number of ket candidates per warp task
 
 struct JKArgs {
     const PairHdr* pairs;
     const PrimPair* prims;
     const PrimPairF* primsf;
-    const int2* tasks;            // (bra pair, first ket candidate)
+    const int4* tasks;            // (bra pair, first ket candidate, end of candidates, 0)
     int ntasks;
     int ket_end;                  // end of the ket class range (exclusive)
     int same_class;               // bra and ket class equal: kets j <= bra
@@ -309,9 +309,9 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
     const int grp = lane / G, sub = lane - (lane / G) * G;
     const int w = blockIdx.x * (JK_THREADS / 32) + wib;
     if (w >= a.ntasks) return;
-    const int2 t = a.tasks[w];
+    const int4 t = a.tasks[w];
     const int ib = t.x;
-    const int jend = min(t.y + JK_RANGE, a.same_class ? ib + 1 : a.ket_end);
+    const int jend = t.z;
     const PairHdr B = a.pairs[ib];
     const float Qb = __ldg(a.Q + ib);
     const float* Dm = a.Dmax;

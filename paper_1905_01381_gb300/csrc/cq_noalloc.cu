@@ -138,7 +138,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
         for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
             a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
             a.counters = cnt + 4 + 4 * qc + 2 * pp;
-            JK_LAUNCH[qc](a, pp, s);
+            launch_jk_class(b, a, qc, pp, s);
         }
     }
     CQ_CUDA(cudaGetLastError());

@@ -146,3 +146,24 @@ def test_zero_density_and_screening(cq):
     J, K, st = b.fock_build(Z, stats=True)
     assert J.abs().max().item() == 0.0 and K.abs().max().item() == 0.0
     assert st["quartets_fp64"] == 0
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_every_class_in_each_kernel_variant(cq, orc, variant):
+    """Lane-group (0) and warp-cooperative (1) kernels for all 21 classes,
+    FP64 and FP32 halves of the mixed build."""
+    mol, bas = CASES["OCNH3"]()
+    b = cq.Basis(mol, bas)
+    for qc in range(21):
+        for p in (0, 1):
+            b.set_variant(qc, p, variant)
+    ob = orc.OBasis(mol, bas)
+    P = synth.density(b.nbf, 9, 15, complex_=True)
+    J, K = b.fock_build(_gpu(P))
+    Jo, Ko = orc.jk(ob, P)
+    assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
+    assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+    Jm, Km, st = b.fock_build(_gpu(P), prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, stats=True)
+    assert st["quartets_fp32"] > 0
+    assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
+    assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
