@@ -165,6 +165,16 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
 int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
 int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
 
+/* Autotuner: times both kernel variants of every class with total angular
+ * momentum >= 4 (lighter classes keep lane groups) on the given density
+ * (device, layout as for cq_fock_build) with the given options (NULL:
+ * mixed precision, mixed_tol 1e-3), keeps the fastest variant per class and
+ * precision in the basis, and returns the choice in table[2*qc + fp32] and
+ * the best kernel time in ms_out[2*qc + fp32] (host arrays of 42, either may
+ * be NULL).  Runs four builds; allocates and frees two output buffers. */
+int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts,
+                int* table, double* ms_out, void* stream);
+
 /* FMA throughput of the current device (FP64 if fp32 == 0, else FP32), in
  * floating-point operations per second (an FMA counts 2), from independent
  * FMA chains on every SM.  Measurement support for the roofline of the

@@ -92,6 +92,7 @@ def lib():
         L.cq_scf.argtypes = [vp, ctypes.c_int, ctypes.POINTER(SCFOpts), vp, vp, vp, ctypes.POINTER(SCFStats), vp]
         L.cq_rt_step.argtypes = [vp, ctypes.POINTER(RTOpts), ctypes.c_int, vp, vp, ctypes.POINTER(RTObs), vp]
         L.cq_dense_info.argtypes = [vp, ip, ip, vp]
+        L.cq_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(FockOpts), ip, dp, vp]
         L.cq_fock_set_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_get_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
@@ -285,3 +286,43 @@ class Basis:
         v = ctypes.c_int()
         check(lib().cq_fock_get_variant(self.h, int(qc), int(fp32), ctypes.byref(v)), "cq_fock_get_variant")
         return v.value
+
+    def autotune(self, P, prec=CQ_PREC_MIXED, mixed_tol=1e-3, schwarz_tol=1e-14, cache=True, stream=None):
+        """Pick the fastest kernel variant per class (see cq_autotune).  With
+        cache=True the choice is stored per GPU model in _build/tuning.json
+        and reused by later calls instead of re-timing."""
+        import json
+        import torch
+        key = torch.cuda.get_device_name()
+        path = os.path.join(_HERE, "_build", "tuning.json")
+        if cache and os.path.exists(path):
+            try:
+                tab = json.load(open(path)).get(key)
+            except Exception:
+                tab = None
+            if tab:
+                for qc, (v64, v32) in enumerate(tab["variant"]):
+                    self.set_variant(qc, 0, v64)
+                    self.set_variant(qc, 1, v32)
+                return tab
+        kind = (CQ_DENS_REAL_SYM if P.dtype == torch.float64 else
+                CQ_DENS_PAULI4 if P.dim() == 3 else CQ_DENS_COMPLEX_HERM)
+        o = FockOpts(schwarz_tol, mixed_tol, prec, 1, 1)
+        tab = (ctypes.c_int * 42)()
+        ms = (ctypes.c_double * 42)()
+        check(lib().cq_autotune(self.h, kind, _ptr(P.contiguous()), ctypes.byref(o), tab, ms,
+                                _stream_ptr(stream)), "cq_autotune")
+        out = {"variant": [[tab[2 * q], tab[2 * q + 1]] for q in range(21)],
+               "best_ms": [[ms[2 * q], ms[2 * q + 1]] for q in range(21)]}
+        if cache:
+            data = {}
+            if os.path.exists(path):
+                try:
+                    data = json.load(open(path))
+                except Exception:
+                    data = {}
+            data[key] = out
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            with open(path, "w") as fh:
+                json.dump(data, fh, indent=1)
+        return out

@@ -73,9 +73,10 @@ def gen_sources():
             src = head + [
                 f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
                 "{",
-                "    const int blocks = (a.ntasks * 32 + JK_THREADS - 1) / JK_THREADS;",
+                f"    const long long warps = (a.qmax + {32 // G} - 1) / {32 // G};",
+                "    const long long blocks = (warps * 32 + JK_THREADS - 1) / JK_THREADS;",
                 "    if (blocks == 0) return;",
-                f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<blocks, JK_THREADS, 0, s>>>(a);",
+                f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<(unsigned)blocks, JK_THREADS, 0, s>>>(a);",
                 "}"]
             if X == Y and tag == "f64":
                 src += [f"void launch_schwarz_{la}{lb}(const JKArgs& a, int begin, int end, float* Qf, double* Qd, cudaStream_t s)",

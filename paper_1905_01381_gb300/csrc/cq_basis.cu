@@ -12,9 +12,13 @@ namespace cq {
 
 const int PC_L[NPC][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
 
-// warp-cooperative kernel for the classes with the largest recurrences:
-// (dp|pp) (dp|ds) (dp|dp) (dd|ps) (dd|pp) (dd|ds) (dd|dp) (dd|dd)
-const int DEFAULT_VARIANT[NQC] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 0, 1, 1, 1, 1, 1};
+// kernel variant per class before tuning (measured on GB300, 210-function
+// s,p,d cluster): the warp-cooperative kernel for the classes with the
+// largest recurrences, (dp|dp) (dd|pp) (dd|dp) (dd|dd) in FP64 and
+// (dd|dp) (dd|dd) in FP32; lane groups elsewhere
+const int DEFAULT_VARIANT[NQC][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
+                                     {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
+                                     {1, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {1, 1}, {1, 1}};
 
 static thread_local std::string g_err;
 
@@ -149,7 +153,8 @@ static void free_basis(cq_basis* b)
     void* ptrs[] = {b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
                     b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
                     b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,
-                    b->d_Kp, b->d_Dmax, b->d_cnt};
+                    b->d_Kp, b->d_Dmax, b->d_cnt, b->d_coop_tasks, b->d_qlist, b->d_qcount,
+                    b->d_task_off, b->d_qoff, b->d_tcount, b->d_toff};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->ev0) cudaEventDestroy(b->ev0);
@@ -175,7 +180,10 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
                        const double* coefs, cq_basis* b)
 {
     CQ_CUDA(cudaGetDevice(&b->device));
-    for (int q = 0; q < NQC; ++q) b->variant[q][0] = b->variant[q][1] = DEFAULT_VARIANT[q];
+    for (int q = 0; q < NQC; ++q) {
+        b->variant[q][0] = DEFAULT_VARIANT[q][0];
+        b->variant[q][1] = DEFAULT_VARIANT[q][1];
+    }
     b->natom = natom;
     b->nsh = nshell;
     b->xyz.assign(xyz, xyz + 3 * natom);
@@ -261,6 +269,13 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
             for (auto& t : tv) tasks.push_back(t.second);
         }
     b->task_off[NQC] = (int)tasks.size();
+    // list regions: one slot per candidate quartet of each class
+    b->qoff.assign(NQC + 1, 0);
+    for (int X = 0, qc = 0; X < NPC; ++X)
+        for (int Y = 0; Y <= X; ++Y, ++qc) {
+            const long long nbra = b->cls_off[X + 1] - b->cls_off[X], nket = b->cls_off[Y + 1] - b->cls_off[Y];
+            b->qoff[qc + 1] = b->qoff[qc] + ((X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket);
+        }
 
     // ---- device copies
     int rc;
@@ -273,6 +288,12 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     if ((rc = upload(&b->d_exps, b->exps))) return rc;
     if ((rc = upload(&b->d_pairs, b->pairs))) return rc;
     if ((rc = upload(&b->d_tasks, tasks))) return rc;
+    if ((rc = upload(&b->d_task_off, b->task_off))) return rc;
+    if ((rc = upload(&b->d_qoff, b->qoff))) return rc;
+    if ((rc = dalloc(&b->d_qlist, (size_t)b->qoff[NQC]))) return rc;
+    if ((rc = dalloc(&b->d_qcount, 2 * NQC))) return rc;
+    if ((rc = dalloc(&b->d_tcount, 2 * tasks.size()))) return rc;
+    if ((rc = dalloc(&b->d_toff, 2 * tasks.size()))) return rc;
     if ((rc = upload(&b->d_axyz, axyz))) return rc;
     if ((rc = upload(&b->d_Z, zc))) return rc;
     if ((rc = dalloc(&b->d_coef, np))) return rc;
@@ -283,7 +304,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     if ((rc = dalloc(&b->d_boysf, (size_t)BOYS_NT * BOYS_F_COLS))) return rc;
     if ((rc = dalloc(&b->d_Qf, b->npair))) return rc;
     if ((rc = dalloc(&b->d_Qd, b->npair))) return rc;
-    if ((rc = dalloc(&b->d_cnt, 4 + 4 * NQC))) return rc;
+    if ((rc = dalloc(&b->d_cnt, 4 + 6 * NQC))) return rc;
     {
         std::vector<double> coefs_raw(coefs, coefs + np);
         double* d_raw = nullptr;
@@ -304,9 +325,52 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     CQ_CUDA(cudaEventCreate(&b->ev1));
     rc = cq_schwarz(b, nullptr, nullptr);
     if (rc) return rc;
+    rc = ensure_coop_tasks(b);
+    if (rc) return rc;
     CQ_CUDA(cudaDeviceSynchronize());
     return CQ_OK;
 }
+
+namespace cq {
+// (bra, ket, [p0, p1)) for every candidate quartet of the classes that use
+// the cooperative kernel, split into chunks of at most COOP_CHUNK primitive
+// quartets; costliest first within a class.
+int ensure_coop_tasks(cq_basis* b)
+{
+    if (!b->coop_dirty) return CQ_OK;
+    std::vector<int4> tasks;
+    b->coop_off.assign(NQC + 1, 0);
+    for (int X = 0, qc = 0; X < NPC; ++X)
+        for (int Y = 0; Y <= X; ++Y, ++qc) {
+            b->coop_off[qc] = (int)tasks.size();
+            if (b->variant[qc][0] != VARIANT_COOP && b->variant[qc][1] != VARIANT_COOP) continue;
+            std::vector<std::pair<int, int4>> tv;
+            for (int i = b->cls_off[X]; i < b->cls_off[X + 1]; ++i) {
+                const int jb = b->cls_off[Y], je = (X == Y) ? i + 1 : b->cls_off[Y + 1];
+                for (int j = jb; j < je; ++j) {
+                    const int np = b->pairs[i].nprim * b->pairs[j].nprim;
+                    for (int p0 = 0; p0 < np; p0 += COOP_CHUNK) {
+                        const int p1 = std::min(np, p0 + COOP_CHUNK);
+                        tv.push_back({p1 - p0, make_int4(i, j, p0, p1)});
+                    }
+                }
+            }
+            std::stable_sort(tv.begin(), tv.end(), [](const std::pair<int, int4>& x, const std::pair<int, int4>& y) {
+                return x.first > y.first;
+            });
+            for (auto& t : tv) tasks.push_back(t.second);
+        }
+    b->coop_off[NQC] = (int)tasks.size();
+    if (b->d_coop_tasks) cudaFree(b->d_coop_tasks);
+    b->d_coop_tasks = nullptr;
+    int rc = dalloc(&b->d_coop_tasks, tasks.size());
+    if (rc) return rc;
+    if (!tasks.empty())
+        CQ_CUDA(cudaMemcpy(b->d_coop_tasks, tasks.data(), tasks.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    b->coop_dirty = false;
+    return CQ_OK;
+}
+}  // namespace cq
 
 extern "C" int cq_basis_create(int natom, const double* xyz, const int* Z, int nshell,
                                const int* shell_atom, const int* shell_L, const int* shell_nprim,

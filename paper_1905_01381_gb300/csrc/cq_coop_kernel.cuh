@@ -21,6 +21,22 @@ __device__ __forceinline__ void boys_rt_any(int L, R T, R* F, const R* tab)
     }
 }
 
+// one vertical-recurrence node: returns the output slot, value in v
+template <typename R>
+__device__ __forceinline__ int coop_node(int shape, const int4 d, const R* __restrict__ cf, const R* V, R& v)
+{
+    const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
+    const int cw = d.w;
+    v = cf[cw & 63] * V[x0];
+    v = fma(cf[(cw >> 6) & 63], V[x1], v);
+    if (shape == 1 || shape == 3) {
+        const int x2 = d.y & 0xffff, x3 = (unsigned)d.y >> 16;
+        v = fma(cf[(cw >> 12) & 63], fma(-cf[(cw >> 18) & 63], V[x3], V[x2]), v);
+    }
+    if (shape >= 2) v = fma(cf[(cw >> 24) & 63], V[d.z & 0xffff], v);
+    return (unsigned)d.z >> 16;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
 {
@@ -33,60 +49,41 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
     R* V = Sb + 32 * (LTOT_MAX + 1);                       // [nslots]
     R* Db = V + nslots_max;                                // 6 density blocks of <= 36
     R* hc = Db + 6 * 36;                                   // AB, CD
-    int* qw = (int*)(hc + 8);                              // queue of 64
 
     const int w = blockIdx.x * COOP_WARPS + wib;
     if (w >= a.ntasks) return;
+    // task: bra pair, ket pair, primitive-quartet range [p0, p1).  HRR and
+    // digestion are linear, so a chunk of primitive quartets is digested on
+    // its own and the J'/K' adds of all chunks sum to the quartet's.
     const int4 t = a.tasks[w];
-    const int ib = t.x;
-    const int jend = t.z;
+    const int ib = t.x, j = t.y, p0 = t.z, p1 = t.w;
     const PairHdr B = a.pairs[ib];
-    const float Qb = __ldg(a.Q + ib);
-    const float* Dm = a.Dmax;
-    const int ns = a.nsh;
-    const float dab_max = __ldg(Dm + B.a * ns + B.b);
+    const PairHdr K = a.pairs[j];
+    {
+        const float* Dm = a.Dmax;
+        const int ns = a.nsh;
+        float m = fmaxf(__ldg(Dm + B.a * ns + B.b), __ldg(Dm + K.a * ns + K.b));
+        m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + K.a), __ldg(Dm + B.a * ns + K.b)));
+        m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + K.a), __ldg(Dm + B.b * ns + K.b)));
+        const float bound = __ldg(a.Q + ib) * __ldg(a.Q + j) * m;
+        bool sel = bound >= a.tau;
+        if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
+        else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
+        if (!sel) return;
+    }
     const int NA = ncart(C.la), NB = ncart(C.lb), NC = ncart(C.lc), ND = ncart(C.ld);
     const R* boys_tab;
     if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
     const int n = a.nbf;
     unsigned long long nq = 0, np = 0;
-    int qn = 0, c0 = t.y;
-    while (true) {
-        while (qn < 1 && c0 < jend) {
-            const int j = c0 + lane;
-            bool sel = false;
-            if (j < jend) {
-                const int kc = __ldg(&a.pairs[j].a), kd = __ldg(&a.pairs[j].b);
-                float m = fmaxf(dab_max, __ldg(Dm + kc * ns + kd));
-                m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + kc), __ldg(Dm + B.a * ns + kd)));
-                m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + kc), __ldg(Dm + B.b * ns + kd)));
-                const float bound = Qb * __ldg(a.Q + j) * m;
-                sel = bound >= a.tau;
-                if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
-                else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
-            }
-            const unsigned msk = __ballot_sync(0xffffffffu, sel);
-            if (sel) qw[qn + __popc(msk & ((1u << lane) - 1u))] = j;
-            qn += __popc(msk);
-            c0 += 32;
-            __syncwarp();
-        }
-        if (qn == 0) break;
-        const int j = qw[0];
-        const int mv = lane + 1 < qn ? qw[lane + 1] : 0;
-        __syncwarp();
-        if (lane + 1 < qn) qw[lane] = mv;
-        __syncwarp();
-        qn -= 1;
-        const PairHdr K = a.pairs[j];
-
+    {
         // ---- primitive quartets: coefficients, VRR, accumulation
         R acc[COOP_MAXACC];
 #pragma unroll
         for (int k = 0; k < COOP_MAXACC; ++k) acc[k] = R(0);
-        const int nkp = K.nprim, tot = B.nprim * K.nprim;
-        for (int base = 0; base < tot; base += 32) {
-            const int cnt = min(32, tot - base);
+        const int nkp = K.nprim;
+        for (int base = p0; base < p1; base += 32) {
+            const int cnt = min(32, p1 - base);
             if (lane < cnt) {
                 const int pq = base + lane;
                 const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
@@ -123,25 +120,22 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                 if (lane <= C.L) V[lane] = Sb[q * (LTOT_MAX + 1) + lane];
                 __syncwarp();
                 const R* cf = coef + q * COOP_NCOEF;
-                for (int g = 0; g < C.nvg; ++g) {
-                    const int4 G = __ldg(C.vgrp + g);
-                    if (lane < G.y) {
-                        const int4 d = __ldg(C.vdesc + G.z + lane);
-                        const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
-                        const int cw = d.w;
-                        R v = cf[cw & 63] * V[x0];
-                        v = fma(cf[(cw >> 6) & 63], V[x1], v);
-                        if (G.x == 1 || G.x == 3) {
-                            const int x2 = d.y & 0xffff, x3 = (unsigned)d.y >> 16;
-                            v = fma(cf[(cw >> 12) & 63], fma(-cf[(cw >> 18) & 63], V[x3], V[x2]), v);
-                        }
-                        if (G.x >= 2) {
-                            const int x4 = d.z & 0xffff;
-                            v = fma(cf[(cw >> 24) & 63], V[x4], v);
-                        }
-                        V[(unsigned)d.z >> 16] = v;
-                    }
-                    if (G.w) __syncwarp();
+                int4 Gn = __ldg(C.vgrp);
+                for (int g = 0; g < C.nvg;) {
+                    const int4 G = Gn;
+                    // the next group of the same level is independent: evaluate both
+                    const bool pair = !G.w && g + 1 < C.nvg;
+                    const int4 G2 = pair ? __ldg(C.vgrp + g + 1) : G;
+                    const int gn = g + (pair ? 2 : 1);
+                    if (gn < C.nvg) Gn = __ldg(C.vgrp + gn);
+                    R v1 = R(0), v2 = R(0);
+                    int o1 = -1, o2 = -1;
+                    if (lane < G.y) o1 = coop_node<R>(G.x, __ldg(C.vdesc + G.z + lane), cf, V, v1);
+                    if (pair && lane < G2.y) o2 = coop_node<R>(G2.x, __ldg(C.vdesc + G2.z + lane), cf, V, v2);
+                    if (o1 >= 0) V[o1] = v1;
+                    if (o2 >= 0) V[o2] = v2;
+                    if ((pair ? G2.w : G.w)) __syncwarp();
+                    g = gn;
                 }
 #pragma unroll
                 for (int k = 0; k < COOP_MAXACC; ++k) {
@@ -262,7 +256,7 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
             nq += __shfl_xor_sync(0xffffffffu, nq, o);
             np += __shfl_xor_sync(0xffffffffu, np, o);
         }
-        if (lane == 0 && nq) {
+        if (lane == 0 && (nq || np)) {
             atomicAdd(a.counters + 0, nq);
             atomicAdd(a.counters + 1, np);
         }

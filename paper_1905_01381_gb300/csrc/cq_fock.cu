@@ -113,10 +113,164 @@ int ensure_scratch(cq_basis* b, int nk)
     return CQ_OK;
 }
 
+// Screening and precision split of the candidates of one static task:
+// returns this lane's class of candidate j0 + lane (-1 rejected, 0 FP64,
+// 1 FP32).
+__device__ __forceinline__ int classify_one(const ClassifyArgs& c, int j, int jend, int ba, int bb, float Qb,
+                                            float dab)
+{
+    if (j >= jend) return -1;
+    const float* Dm = c.Dmax;
+    const int ns = c.nsh;
+    const int kc = __ldg(&c.pairs[j].a), kd = __ldg(&c.pairs[j].b);
+    float m = fmaxf(dab, __ldg(Dm + kc * ns + kd));
+    m = fmaxf(m, fmaxf(__ldg(Dm + ba * ns + kc), __ldg(Dm + ba * ns + kd)));
+    m = fmaxf(m, fmaxf(__ldg(Dm + bb * ns + kc), __ldg(Dm + bb * ns + kd)));
+    const float bound = Qb * __ldg(c.Q + j) * m;
+    if (!(bound >= c.tau)) return -1;
+    return (c.split && bound < c.tau_mixed) ? 1 : 0;
+}
+
+// Pass 1 (write = 0): survivors per task and precision -> tcount[2t + p].
+// Pass 3 (write = 1): survivors written at the scanned offsets, in task
+// order and, within a task, in ket order, so that a warp of the integral
+// kernels gets consecutive kets of mostly one bra with similar primitive
+// counts.  FP64 entries fill a class's region from the front, FP32 entries
+// from the back.
+__global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsigned int* __restrict__ tcount,
+                                const unsigned int* __restrict__ toff)
+{
+    const int lane = threadIdx.x & 31;
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= c.ntasks) return;
+    int qc = 0;
+    while (qc + 1 < nqc && c.cls_task_off[qc + 1] <= w) ++qc;
+    const int4 t = c.tasks[w];
+    const int ib = t.x;
+    const int ba = __ldg(&c.pairs[ib].a), bb = __ldg(&c.pairs[ib].b);
+    const float Qb = __ldg(c.Q + ib);
+    const float dab = __ldg(c.Dmax + ba * c.nsh + bb);
+    const long long base = c.cls_qoff[qc], top = c.cls_qoff[qc + 1];
+    unsigned int n0 = 0, n1 = 0;
+    unsigned int o0 = write ? toff[2 * w] : 0, o1 = write ? toff[2 * w + 1] : 0;
+    for (int j0 = t.y; j0 < t.z; j0 += 32) {
+        const int j = j0 + lane;
+        const int prec = classify_one(c, j, t.z, ba, bb, Qb, dab);
+        const unsigned m0 = __ballot_sync(0xffffffffu, prec == 0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, prec == 1);
+        if (write) {
+            const unsigned below = (1u << lane) - 1u;
+            if (prec == 0) c.qlist[base + o0 + n0 + __popc(m0 & below)] = make_int2(ib, j);
+            if (prec == 1) c.qlist[top - 1 - (o1 + n1 + __popc(m1 & below))] = make_int2(ib, j);
+        }
+        n0 += __popc(m0);
+        n1 += __popc(m1);
+    }
+    if (!write && lane == 0) {
+        tcount[2 * w] = n0;
+        tcount[2 * w + 1] = n1;
+    }
+}
+
+// Pass 2: per class (one CTA each), exclusive scan of the task counts into
+// offsets within the class's region, and the list lengths.
+__global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const unsigned int* __restrict__ tcount,
+                                  unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
+{
+    __shared__ unsigned int part[2][1024];
+    const int qc = blockIdx.x;
+    const int t0 = cls_task_off[qc], t1 = cls_task_off[qc + 1];
+    const int n = t1 - t0;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int b0 = t0 + threadIdx.x * per, b1 = min(t1, b0 + per);
+    unsigned int s0 = 0, s1 = 0;
+    for (int t = b0; t < b1; ++t) { s0 += tcount[2 * t]; s1 += tcount[2 * t + 1]; }
+    part[0][threadIdx.x] = s0;
+    part[1][threadIdx.x] = s1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int a0 = 0, a1 = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const unsigned int x0 = part[0][i], x1 = part[1][i];
+            part[0][i] = a0; part[1][i] = a1;
+            a0 += x0; a1 += x1;
+        }
+        qcount[2 * qc] = a0;
+        qcount[2 * qc + 1] = a1;
+    }
+    __syncthreads();
+    unsigned int a0 = part[0][threadIdx.x], a1 = part[1][threadIdx.x];
+    for (int t = b0; t < b1; ++t) {
+        toff[2 * t] = a0; toff[2 * t + 1] = a1;
+        a0 += tcount[2 * t]; a1 += tcount[2 * t + 1];
+    }
+}
+
+// Screen and split every candidate quartet into the per-class lists (one
+// kernel), then launch every class kernel, heaviest classes first.
+int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s)
+{
+    ClassifyArgs c;
+    c.pairs = b->d_pairs; c.tasks = b->d_tasks; c.ntasks = b->task_off[NQC];
+    c.cls_task_off = b->d_task_off; c.cls_qoff = b->d_qoff;
+    c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->nsh;
+    c.tau = a.tau; c.tau_mixed = a.tau_mixed; c.split = o.prec == CQ_PREC_MIXED;
+    c.qlist = b->d_qlist; c.qcount = b->d_qcount;
+    if (c.ntasks > 0) {
+        const int blocks = (c.ntasks * 32 + 255) / 256;
+        classify_kernel<<<blocks, 256, 0, s>>>(c, NQC, 0, b->d_tcount, nullptr);
+        scan_tasks_kernel<<<NQC, 1024, 0, s>>>(b->d_task_off, b->d_tcount, b->d_toff, b->d_qcount);
+        classify_kernel<<<blocks, 256, 0, s>>>(c, NQC, 1, nullptr, b->d_toff);
+    }
+    CQ_CUDA(cudaGetLastError());
+    static const int order[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
+    cq_basis* bm = const_cast<cq_basis*>(b);
+    for (int oi = 0; oi < NQC; ++oi) {
+        const int qc = order[oi];
+        int X = 0;
+        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+        const int Y = qc - X * (X + 1) / 2;
+        a.tasks = b->d_tasks + b->task_off[qc];
+        a.ntasks = b->task_off[qc + 1] - b->task_off[qc];
+        a.qmax = b->qoff[qc + 1] - b->qoff[qc];
+        if (a.ntasks == 0 || a.qmax == 0) continue;
+        a.ket_end = b->cls_off[Y + 1];
+        a.same_class = (X == Y);
+        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
+            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
+            a.qlist = pp == 0 ? b->d_qlist + b->qoff[qc] : b->d_qlist + (b->qoff[qc + 1] - 1);
+            a.qdir = pp == 0 ? 1 : -1;
+            a.qcount = b->d_qcount + 2 * qc + pp;
+            unsigned long long* base_cnt = a.counters;
+            a.counters = base_cnt + 4 * qc + 2 * pp;
+            if (profile) {
+                for (int e = 0; e < 2; ++e)
+                    if (!bm->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&bm->pev[qc][pp][e]));
+                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][0], s));
+            }
+            launch_jk_class(b, a, qc, pp, s);
+            if (profile) {
+                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][1], s));
+                bm->pev_used[qc][pp] = true;
+            }
+            a.counters = base_cnt;
+        }
+    }
+    return CQ_OK;
+}
+
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s)
 {
-    if (b->variant[qc][fp32] == VARIANT_COOP) launch_coop(a, qc, fp32, s);
-    else JK_LAUNCH[qc](a, fp32, s);
+    // a class switched to the cooperative kernel uses it once its task list
+    // has been rebuilt (by the next cq_fock_build); until then, lane groups
+    if (b->variant[qc][fp32] == VARIANT_COOP && !b->coop_dirty) {
+        JKArgs c = a;
+        c.tasks = b->d_coop_tasks + b->coop_off[qc];
+        c.ntasks = b->coop_off[qc + 1] - b->coop_off[qc];
+        if (c.ntasks > 0) launch_coop(c, qc, fp32, s);
+    } else {
+        JK_LAUNCH[qc](a, fp32, s);
+    }
 }
 
 }  // namespace cq
@@ -129,6 +283,7 @@ extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
         set_error("cq_fock_set_variant: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
+    if (b->variant[qc][fp32] != variant) b->coop_dirty = true;
     b->variant[qc][fp32] = variant;
     return CQ_OK;
 }
@@ -168,6 +323,7 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     const int nk = nk_of(kind);
     int rc = ensure_scratch(b, nk);
     if (rc) return rc;
+    if ((rc = ensure_coop_tasks(b))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     const int n = b->nbf;
     const size_t nn = (size_t)n * n;
@@ -177,7 +333,7 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, b->d_Dp, b->d_Dmax);
     CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
-    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 4 * NQC) * sizeof(unsigned long long), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
     if (b->profile) memset(b->pev_used, 0, sizeof b->pev_used);
     JKArgs a;
     memset(&a, 0, sizeof a);
@@ -189,33 +345,9 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     a.want_j = o.want_J; a.want_k = o.want_K;
     a.J = b->d_Jp; a.K = b->d_Kp;
     a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
-    // heaviest classes first
-    static const int order[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
-    for (int oi = 0; oi < NQC; ++oi) {
-        const int qc = order[oi];
-        int X = 0;
-        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
-        const int Y = qc - X * (X + 1) / 2;
-        a.tasks = b->d_tasks + b->task_off[qc];
-        a.ntasks = b->task_off[qc + 1] - b->task_off[qc];
-        if (a.ntasks == 0) continue;
-        a.ket_end = b->cls_off[Y + 1];
-        a.same_class = (X == Y);
-        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
-            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
-            a.counters = b->d_cnt + 4 + 4 * qc + 2 * pp;
-            if (b->profile) {
-                for (int e = 0; e < 2; ++e)
-                    if (!b->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&b->pev[qc][pp][e]));
-                CQ_CUDA(cudaEventRecord(b->pev[qc][pp][0], s));
-            }
-            launch_jk_class(b, a, qc, pp, s);
-            if (b->profile) {
-                CQ_CUDA(cudaEventRecord(b->pev[qc][pp][1], s));
-                b->pev_used[qc][pp] = true;
-            }
-        }
-    }
+    a.counters = b->d_cnt + 4;
+    rc = classify_and_launch(b, a, o, b->profile != 0, s);
+    if (rc) return rc;
     CQ_CUDA(cudaGetLastError());
     counter_total_kernel<<<1, 32, 0, s>>>(b->d_cnt);
     finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, b->d_Jp, b->d_Kp, J, (double*)K, o.want_J, o.want_K);
@@ -262,4 +394,69 @@ extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, un
         *ms = t;
     }
     return CQ_OK;
+}
+
+// Autotuner: time every kernel variant of every class on the caller's
+// density (one profiled build per variant after a warm-up build), keep the
+// fastest per class and precision.  Light classes (total angular momentum
+// below 4) stay on lane groups: one contracted quartet per warp cannot pay
+// off there.
+extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts, int* table,
+                           double* ms_out, void* stream)
+{
+    if (!b || !P) { set_error("cq_autotune: NULL argument"); return CQ_ERR_INVALID_ARG; }
+    cq_fock_opts o{1e-14, 1e-3, CQ_PREC_MIXED, 1, 1};
+    if (opts) o = *opts;
+    const int n = b->nbf;
+    const size_t nn = (size_t)n * n;
+    const int nk = nk_of(kind);
+    double *J = nullptr, *K = nullptr;
+    int rc;
+    if ((rc = dalloc(&J, nn))) return rc;
+    if ((rc = dalloc(&K, nn * (nk == 1 ? 1 : nk == 2 ? 2 : 8)))) { cudaFree(J); return rc; }
+    const int old_profile = b->profile;
+    b->profile = 1;
+    double best[NQC][2];
+    int choice[NQC][2];
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < 2; ++p) { best[q][p] = 1e300; choice[q][p] = b->variant[q][p]; }
+    auto Lof = [](int qc) {
+        int X = 0;
+        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+        const int Y = qc - X * (X + 1) / 2;
+        return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
+    };
+    for (int v = 0; v < 2 && rc == CQ_OK; ++v) {
+        for (int q = 0; q < NQC; ++q)
+            for (int p = 0; p < 2; ++p) {
+                const int want = (Lof(q) >= 4) ? v : VARIANT_LANES;
+                if (b->variant[q][p] != want) b->coop_dirty = true;
+                b->variant[q][p] = want;
+            }
+        for (int rep = 0; rep < 2 && rc == CQ_OK; ++rep) {
+            cq_fock_stats st;
+            rc = cq_fock_build(b, kind, P, J, K, &o, &st, stream);
+        }
+        if (rc) break;
+        for (int q = 0; q < NQC; ++q)
+            for (int p = 0; p < 2; ++p) {
+                if (Lof(q) < 4 && v == VARIANT_COOP) continue;
+                double ms = 0.0;
+                unsigned long long nq = 0, np = 0;
+                if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &np))) break;
+                if (ms < best[q][p]) { best[q][p] = ms; choice[q][p] = v; }
+            }
+    }
+    b->profile = old_profile;
+    cudaFree(J);
+    cudaFree(K);
+    if (rc) return rc;
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < 2; ++p) {
+            if (b->variant[q][p] != choice[q][p]) b->coop_dirty = true;
+            b->variant[q][p] = choice[q][p];
+            if (table) table[2 * q + p] = choice[q][p];
+            if (ms_out) ms_out[2 * q + p] = best[q][p] < 1e299 ? best[q][p] : 0.0;
+        }
+    return ensure_coop_tasks(b);
 }

@@ -27,7 +27,7 @@ size_t coop_smem_bytes(int qc, int fp32);
 
 // kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative
 constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1;
-extern const int DEFAULT_VARIANT[NQC];
+extern const int DEFAULT_VARIANT[NQC][2];
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
@@ -116,10 +116,27 @@ struct cq_basis {
     std::vector<void*> dense_bufs; // other driver scratch, freed with the basis
     void* rt = nullptr;            // RT-TDHF buffers (cq_drivers.cu)
     int variant[cq::NQC][2] = {};  // kernel variant per class and precision
+    // tasks of the warp-cooperative kernel: (bra, ket, primitive range), built
+    // for the classes that use it, rebuilt when the variant table changes
+    std::vector<int> coop_off;     // NQC + 1
+    // compacted quartet lists (per class: FP64 from the front, FP32 from the
+    // back of its region), rebuilt on the device by every build
+    std::vector<long long> qoff;   // NQC + 1
+    int2* d_qlist = nullptr;
+    unsigned int* d_qcount = nullptr;   // [NQC][2]
+    int* d_task_off = nullptr;          // NQC + 1 (device copy)
+    long long* d_qoff = nullptr;        // NQC + 1 (device copy)
+    unsigned int* d_tcount = nullptr;   // 2 per task: survivors per precision
+    unsigned int* d_toff = nullptr;     // 2 per task: offsets in the class lists
+    int4* d_coop_tasks = nullptr;
+    bool coop_dirty = true;
 };
 
 namespace cq {
+constexpr int COOP_CHUNK = 64;   // primitive quartets per cooperative task
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s);
+int ensure_coop_tasks(cq_basis* b);
+int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s);
 }
 
 namespace cq {

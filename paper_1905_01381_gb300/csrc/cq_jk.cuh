@@ -32,6 +32,10 @@ struct JKArgs {
     const double* boys_d;
     const float* boys_f;
     unsigned long long* counters; // [0] quartets, [1] primitive quartets
+    const int2* qlist;            // compacted (bra, ket) quartets of this class and precision
+    const unsigned int* qcount;   // number of entries (device)
+    int qdir;                     // +1: entries qlist[i]; -1: entries qlist[-i] (list filled from the back)
+    long long qmax;               // capacity of the list (candidate quartets of the class)
 };
 
 template <typename R>
@@ -127,7 +131,7 @@ __device__ __forceinline__ float dmax6(const float* Dm, int nsh, int a, int b, i
 // half-accumulation convention: J = J' + J'^T, K = K' +/- K'^T).
 template <int LA, int LB, int LC, int LD, typename R>
 __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const R* __restrict__ I,
-                                       R sdeg, const JKArgs& a, double* __restrict__ jab)
+                                       R sdeg, const JKArgs& a, double* __restrict__ jq)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     const int n = a.nbf;
@@ -155,7 +159,7 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
                 t = fma(v, dcd[ls], t);
                 jcd[ls] = fma(v, dab[mn], jcd[ls]);
             }
-            jab[mn] = fma(2.0 * (double)sdeg, (double)t, jab[mn]);
+            jq[mn] = 2.0 * (double)sdeg * (double)t;
         }
         const double f = 2.0 * (double)sdeg;
 #pragma unroll
@@ -220,10 +224,10 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
 
 // Digestion of the integral subset owned by one lane of a G-lane group
 // (bra function pairs mn = sub, sub+G, ...).  Adds the lane's partial J'_cd
-// and K' blocks to jcd / kblk (zeroed by the caller) and its J'_ab part to jab.
+// and K' blocks to jcd / kblk (zeroed by the caller) and adds its J'_ab elements.
 template <int LA, int LB, int LC, int LD, typename R, int G>
 __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, const R* __restrict__ I,
-                                            R sdeg, const JKArgs& a, int q, int sub, double* __restrict__ jab,
+                                            R sdeg, const JKArgs& a, int q, int sub,
                                             R* __restrict__ jcd, R* __restrict__ kblk)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
@@ -252,7 +256,7 @@ __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, 
                 t = fma(v, dcd[ls], t);
                 jcd[ls] = fma(v, dab, jcd[ls]);
             }
-            jab[mn] = fma(2.0 * (double)sdeg, (double)t, jab[mn]);
+            atomicAdd(a.J + (size_t)(fa + m) * n + fb + k, 2.0 * (double)sdeg * (double)t);
         }
     }
     if (a.want_k) {
@@ -292,11 +296,30 @@ __device__ __forceinline__ T group_sum(T v)
     return v;
 }
 
-// Lane-group variant: a group of G lanes evaluates one contracted quartet,
-// its lanes splitting the primitive quartets; accumulators and digested
-// blocks are summed across the group with shuffles.  Kets that survive
-// screening (and belong to this kernel's precision) are compacted through a
-// per-warp queue in shared memory so that no group idles on a rejected ket.
+// Screening and precision split of every candidate quartet (one warp per
+// static task of candidates): survivors are appended, warp-aggregated, to the
+// class's FP64 list (from the front of its region) or FP32 list (from the
+// back).  cls_task_off/cls_qoff: per-class offsets of tasks and list regions.
+struct ClassifyArgs {
+    const PairHdr* pairs;
+    const int4* tasks;
+    int ntasks;
+    const int* cls_task_off;      // NQC + 1
+    const long long* cls_qoff;    // NQC + 1
+    const float* Q;
+    const float* Dmax;
+    int nsh;
+    float tau, tau_mixed;
+    int split;                    // 0: every survivor to the FP64 list
+    int2* qlist;
+    unsigned int* qcount;         // [NQC][2]
+};
+
+// Lane-group kernel over a compacted quartet list: a group of G lanes
+// evaluates one contracted quartet, its lanes splitting the primitive
+// quartets; accumulators and digested blocks are summed across the group
+// with shuffles.  Warp w takes list entries [w*S, w*S + S), S = 32/G; warps
+// beyond the device-side count return at once.
 template <int LA, int LB, int LC, int LD, typename R, int G>
 __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
 {
@@ -304,165 +327,140 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
     constexpr int NKB = NA * NC + NA * ND + NB * NC + NB * ND;
     constexpr int S = 32 / G;
     using C = EriClass<LA, LB, LC, LD>;
-    __shared__ int queue[JK_THREADS / 32][64];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane - (lane / G) * G;
-    const int w = blockIdx.x * (JK_THREADS / 32) + wib;
-    if (w >= a.ntasks) return;
-    const int4 t = a.tasks[w];
-    const int ib = t.x;
-    const int jend = t.z;
-    const PairHdr B = a.pairs[ib];
-    const float Qb = __ldg(a.Q + ib);
-    const float* Dm = a.Dmax;
-    const int ns = a.nsh;
-    const float dab_max = __ldg(Dm + B.a * ns + B.b);
-    double jab[NA * NB];
+    const long long w = ((long long)blockIdx.x * JK_THREADS + threadIdx.x) >> 5;
+    const long long cnt = (long long)*a.qcount;
+    if (w * S >= cnt) return;
+    const long long idx = w * S + grp;
+    const bool on = idx < cnt;
+    const int2 e = a.qlist[(on ? idx : w * S) * a.qdir];
+    const PairHdr B = a.pairs[e.x];
+    const PairHdr K = a.pairs[e.y];
+    R acc[C::NACC];
 #pragma unroll
-    for (int i = 0; i < NA * NB; ++i) jab[i] = 0.0;
-    int* qw = queue[wib];
-    int qn = 0;
-    int c0 = t.y;
+    for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
     unsigned long long nq = 0, np = 0;
-    while (true) {
-        while (qn < S && c0 < jend) {
-            const int j = c0 + lane;
-            bool sel = false;
-            if (j < jend) {
-                const int kc = __ldg(&a.pairs[j].a), kd = __ldg(&a.pairs[j].b);
-                float m = fmaxf(dab_max, __ldg(Dm + kc * ns + kd));
-                m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + kc), __ldg(Dm + B.a * ns + kd)));
-                m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + kc), __ldg(Dm + B.b * ns + kd)));
-                const float bound = Qb * __ldg(a.Q + j) * m;
-                sel = bound >= a.tau;
-                if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
-                else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
-            }
-            const unsigned msk = __ballot_sync(0xffffffffu, sel);
-            if (sel) qw[qn + __popc(msk & ((1u << lane) - 1u))] = j;
-            qn += __popc(msk);
-            c0 += 32;
-            __syncwarp();
+    if (on) {
+        const R* boys_tab;
+        if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
+        const int nkp = K.nprim, tot = B.nprim * K.nprim;
+        for (int pq = sub; pq < tot; pq += G) {
+            const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
+            PrimPairT<R> bp, kp;
+            load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+            load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+            prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
         }
-        if (qn == 0) break;
-        const int cnt = min(S, qn);
-        const bool on = grp < cnt;
-        const int j = on ? qw[grp] : ib;
-        const int rem = qn - cnt;
-        const int mv = lane < rem ? qw[cnt + lane] : 0;
-        __syncwarp();
-        if (lane < rem) qw[lane] = mv;
-        __syncwarp();
-        qn = rem;
-
-        const PairHdr K = a.pairs[j];
-        R acc[C::NACC];
-#pragma unroll
-        for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
-        if (on) {
-            const R* boys_tab;
-            if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
-            const int nkp = K.nprim, tot = B.nprim * K.nprim;
-            for (int pq = sub; pq < tot; pq += G) {
-                const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
-                PrimPairT<R> bp, kp;
-                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
-                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-                prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
-            }
-            if (sub == 0) { nq += 1; np += (unsigned long long)tot; }
-        }
-        if constexpr (G > 1) {
-#pragma unroll
-            for (int i = 0; i < C::NACC; ++i) acc[i] = group_sum<R, G>(acc[i]);
-        }
-        R sdeg = R(1);
-        if (B.a == B.b) sdeg *= R(0.5);
-        if (K.a == K.b) sdeg *= R(0.5);
-        if (j == ib) sdeg *= R(0.5);
-        if constexpr (G == 1) {
-            if (on) {
-                R I[C::N];
-                R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
-                R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
-                C::template hrr<R>(acc, ABv, CDv, I);
-                digest<LA, LB, LC, LD, R>(B, K, I, sdeg, a, jab);
-            }
-        } else {
-            R I[C::N];
-            if (on) {
-                R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
-                R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
-                C::template hrr<R>(acc, ABv, CDv, I);
-            }
-            const int n = a.nbf;
-            const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
-#pragma unroll 1
-            for (int q = 0; q < a.nk; ++q) {
-                if (q > 0 && !a.want_k) break;
-                R jcd[NC * ND], kb[NKB];
-#pragma unroll
-                for (int i = 0; i < NC * ND; ++i) jcd[i] = R(0);
-#pragma unroll
-                for (int i = 0; i < NKB; ++i) kb[i] = R(0);
-                if (on) digest_part<LA, LB, LC, LD, R, G>(B, K, I, sdeg, a, q, sub, jab, jcd, kb);
-                if (q == 0 && a.want_j) {
-                    const double f = 2.0 * (double)sdeg;
-#pragma unroll
-                    for (int l = 0; l < NC; ++l)
-#pragma unroll
-                        for (int s = 0; s < ND; ++s) {
-                            const R v = group_sum<R, G>(jcd[l * ND + s]);
-                            if (on && ((l * ND + s) % G) == sub)
-                                atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)v);
-                        }
-                }
-                if (a.want_k) {
-                    double* Kq = a.K + (size_t)q * n * n;
-                    const double f = (double)sdeg;
-                    int e = 0;
-#pragma unroll
-                    for (int m = 0; m < NA; ++m)
-#pragma unroll
-                        for (int l = 0; l < NC; ++l, ++e) {
-                            const R v = group_sum<R, G>(kb[m * NC + l]);
-                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)v);
-                        }
-#pragma unroll
-                    for (int m = 0; m < NA; ++m)
-#pragma unroll
-                        for (int s = 0; s < ND; ++s, ++e) {
-                            const R v = group_sum<R, G>(kb[NA * NC + m * ND + s]);
-                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)v);
-                        }
-#pragma unroll
-                    for (int k = 0; k < NB; ++k)
-#pragma unroll
-                        for (int l = 0; l < NC; ++l, ++e) {
-                            const R v = group_sum<R, G>(kb[NA * NC + NA * ND + k * NC + l]);
-                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)v);
-                        }
-#pragma unroll
-                    for (int k = 0; k < NB; ++k)
-#pragma unroll
-                        for (int s = 0; s < ND; ++s, ++e) {
-                            const R v = group_sum<R, G>(kb[NA * NC + NA * ND + NB * NC + k * ND + s]);
-                            if (on && (e % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)v);
-                        }
-                }
-            }
-        }
+        if (sub == 0) { nq = 1; np = (unsigned long long)tot; }
     }
-    // warp reduction of the bra J' block, one writer per warp
-    if (a.want_j) {
+    if constexpr (G > 1) {
 #pragma unroll
-        for (int i = 0; i < NA * NB; ++i) {
-            double v = jab[i];
+        for (int i = 0; i < C::NACC; ++i) acc[i] = group_sum<R, G>(acc[i]);
+    }
+    R sdeg = R(1);
+    if (B.a == B.b) sdeg *= R(0.5);
+    if (K.a == K.b) sdeg *= R(0.5);
+    if (e.x == e.y) sdeg *= R(0.5);
+    if constexpr (G == 1) {
+        double jq[NA * NB];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0 && v != 0.0) {
-                const int m = i / NB, k = i % NB;
-                atomicAdd(a.J + (size_t)(B.bfa + m) * a.nbf + B.bfb + k, v);
+        for (int i = 0; i < NA * NB; ++i) jq[i] = 0.0;
+        if (on) {
+            R I[C::N];
+            R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
+            R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
+            C::template hrr<R>(acc, ABv, CDv, I);
+            digest<LA, LB, LC, LD, R>(B, K, I, sdeg, a, jq);
+        }
+        if (a.want_j) {
+            // J'_ab: segmented warp sum over runs of lanes with the same bra
+            // pair (list entries of one bra are contiguous), one add per run
+            const int my = on ? e.x : -1;
+            const int prev = __shfl_up_sync(0xffffffffu, my, 1);
+            const bool head = lane == 0 || prev != my;
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            const int seg = __popc(heads & (0xffffffffu >> (31 - lane)));
+            bool same[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) {
+                const int o = 1 << k;
+                const int so = __shfl_down_sync(0xffffffffu, seg, o);
+                same[k] = (lane + o < 32) && so == seg;
+            }
+#pragma unroll
+            for (int i = 0; i < NA * NB; ++i) {
+                double v = jq[i];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    const double u = __shfl_down_sync(0xffffffffu, v, 1 << k);
+                    if (same[k]) v += u;
+                }
+                if (head && on && v != 0.0)
+                    atomicAdd(a.J + (size_t)(B.bfa + i / NB) * a.nbf + B.bfb + i % NB, v);
+            }
+        }
+    } else {
+        R I[C::N];
+        if (on) {
+            R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
+            R CDv[3] = {(R)K.AB[0], (R)K.AB[1], (R)K.AB[2]};
+            C::template hrr<R>(acc, ABv, CDv, I);
+        }
+        const int n = a.nbf;
+        const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+#pragma unroll 1
+        for (int q = 0; q < a.nk; ++q) {
+            if (q > 0 && !a.want_k) break;
+            R jcd[NC * ND], kb[NKB];
+#pragma unroll
+            for (int i = 0; i < NC * ND; ++i) jcd[i] = R(0);
+#pragma unroll
+            for (int i = 0; i < NKB; ++i) kb[i] = R(0);
+            if (on) digest_part<LA, LB, LC, LD, R, G>(B, K, I, sdeg, a, q, sub, jcd, kb);
+            if (q == 0 && a.want_j) {
+                const double f = 2.0 * (double)sdeg;
+#pragma unroll
+                for (int l = 0; l < NC; ++l)
+#pragma unroll
+                    for (int s = 0; s < ND; ++s) {
+                        const R v = group_sum<R, G>(jcd[l * ND + s]);
+                        if (on && ((l * ND + s) % G) == sub)
+                            atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)v);
+                    }
+            }
+            if (a.want_k) {
+                double* Kq = a.K + (size_t)q * n * n;
+                const double f = (double)sdeg;
+                int e2 = 0;
+#pragma unroll
+                for (int m = 0; m < NA; ++m)
+#pragma unroll
+                    for (int l = 0; l < NC; ++l, ++e2) {
+                        const R v = group_sum<R, G>(kb[m * NC + l]);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)v);
+                    }
+#pragma unroll
+                for (int m = 0; m < NA; ++m)
+#pragma unroll
+                    for (int s = 0; s < ND; ++s, ++e2) {
+                        const R v = group_sum<R, G>(kb[NA * NC + m * ND + s]);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)v);
+                    }
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+#pragma unroll
+                    for (int l = 0; l < NC; ++l, ++e2) {
+                        const R v = group_sum<R, G>(kb[NA * NC + NA * ND + k * NC + l]);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)v);
+                    }
+#pragma unroll
+                for (int k = 0; k < NB; ++k)
+#pragma unroll
+                    for (int s = 0; s < ND; ++s, ++e2) {
+                        const R v = group_sum<R, G>(kb[NA * NC + NA * ND + NB * NC + k * ND + s]);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)v);
+                    }
             }
         }
     }

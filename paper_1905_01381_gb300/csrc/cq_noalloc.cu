@@ -67,7 +67,7 @@ extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
     const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
     const size_t nn = (size_t)nbf * nbf;
     return round256(nn * nk * sizeof(double)) * 2 + round256(nn * sizeof(double)) +
-           round256((size_t)nshell * nshell * sizeof(float)) + round256((4 + 4 * NQC) * sizeof(unsigned long long));
+           round256((size_t)nshell * nshell * sizeof(float)) + round256((4 + 6 * NQC) * sizeof(unsigned long long));
 }
 
 extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, double* J, void* K,
@@ -115,7 +115,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     // the array keeps the previous call's contents: clear the accumulators
     CQ_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(Kp, 0, nn * nk * sizeof(double), s));
-    CQ_CUDA(cudaMemsetAsync(cnt, 0, (4 + 4 * NQC) * sizeof(unsigned long long), s));
+    CQ_CUDA(cudaMemsetAsync(cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
@@ -126,21 +126,9 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     a.want_j = o.want_J; a.want_k = o.want_K;
     a.J = Jp; a.K = Kp;
     a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
-    for (int qc = NQC - 1; qc >= 0; --qc) {
-        int X = 0;
-        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
-        const int Y = qc - X * (X + 1) / 2;
-        a.tasks = b->d_tasks + b->task_off[qc];
-        a.ntasks = b->task_off[qc + 1] - b->task_off[qc];
-        if (a.ntasks == 0) continue;
-        a.ket_end = b->cls_off[Y + 1];
-        a.same_class = (X == Y);
-        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
-            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
-            a.counters = cnt + 4 + 4 * qc + 2 * pp;
-            launch_jk_class(b, a, qc, pp, s);
-        }
-    }
+    a.counters = cnt + 4;
+    rc = classify_and_launch(b, a, o, false, s);
+    if (rc) return rc;
     CQ_CUDA(cudaGetLastError());
     finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, Jp, Kp, J, (double*)K, o.want_J, o.want_K);
     CQ_CUDA(cudaGetLastError());

@@ -167,3 +167,16 @@ def test_every_class_in_each_kernel_variant(cq, orc, variant):
     assert st["quartets_fp32"] > 0
     assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
     assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
+
+
+def test_autotune_keeps_parity(cq, orc):
+    mol, bas = CASES["OCNH3"]()
+    b = cq.Basis(mol, bas)
+    P = synth.density(b.nbf, 9, 16, complex_=True)
+    tab = b.autotune(_gpu(P), cache=False)
+    assert len(tab["variant"]) == 21
+    assert all(v in (0, 1) for row in tab["variant"] for v in row)
+    J, K = b.fock_build(_gpu(P))
+    Jo, Ko = orc.jk(orc.OBasis(mol, bas), P)
+    assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
+    assert np.abs(K.cpu().numpy() - Ko).max() < TOL
