@@ -163,6 +163,11 @@ static void free_basis(cq_basis* b)
         for (int p = 0; p < 2; ++p)
             for (int e = 0; e < 2; ++e)
                 if (b->pev[q][p][e]) cudaEventDestroy(b->pev[q][p][e]);
+    for (int k = 0; k < cq_basis::NSIDE; ++k) {
+        if (b->side[k]) cudaStreamDestroy(b->side[k]);
+        if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
+    }
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
     delete b;
 }
 
@@ -323,6 +328,11 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     CQ_CUDA(cudaGetLastError());
     CQ_CUDA(cudaEventCreate(&b->ev0));
     CQ_CUDA(cudaEventCreate(&b->ev1));
+    CQ_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+    for (int k = 0; k < cq_basis::NSIDE; ++k) {
+        CQ_CUDA(cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking));
+        CQ_CUDA(cudaEventCreateWithFlags(&b->join_ev[k], cudaEventDisableTiming));
+    }
     rc = cq_schwarz(b, nullptr, nullptr);
     if (rc) return rc;
     rc = ensure_coop_tasks(b);

@@ -225,6 +225,15 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     CQ_CUDA(cudaGetLastError());
     static const int order[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
     cq_basis* bm = const_cast<cq_basis*>(b);
+    // fork: the class kernels are independent (they only add into J'/K'), so
+    // they run on side streams that wait for the classification; the main
+    // stream joins them before finalisation.  A profiled build stays on one
+    // stream so that each class's events time that class alone.
+    const bool fork = !profile;
+    if (fork) CQ_CUDA(cudaEventRecord(bm->fork_ev, s));
+    if (fork)
+        for (int k = 0; k < cq_basis::NSIDE; ++k) CQ_CUDA(cudaStreamWaitEvent(bm->side[k], bm->fork_ev, 0));
+    int launched = 0;
     for (int oi = 0; oi < NQC; ++oi) {
         const int qc = order[oi];
         int X = 0;
@@ -248,7 +257,9 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
                     if (!bm->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&bm->pev[qc][pp][e]));
                 CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][0], s));
             }
-            launch_jk_class(b, a, qc, pp, s);
+            cudaStream_t ks = fork ? bm->side[launched % cq_basis::NSIDE] : s;
+            ++launched;
+            launch_jk_class(b, a, qc, pp, ks);
             if (profile) {
                 CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][1], s));
                 bm->pev_used[qc][pp] = true;
@@ -256,6 +267,11 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
             a.counters = base_cnt;
         }
     }
+    if (fork)
+        for (int k = 0; k < cq_basis::NSIDE; ++k) {
+            CQ_CUDA(cudaEventRecord(bm->join_ev[k], bm->side[k]));
+            CQ_CUDA(cudaStreamWaitEvent(s, bm->join_ev[k], 0));
+        }
     return CQ_OK;
 }
 

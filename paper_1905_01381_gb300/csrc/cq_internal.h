@@ -128,6 +128,11 @@ struct cq_basis {
     long long* d_qoff = nullptr;        // NQC + 1 (device copy)
     unsigned int* d_tcount = nullptr;   // 2 per task: survivors per precision
     unsigned int* d_toff = nullptr;     // 2 per task: offsets in the class lists
+    // side streams for running the class kernels of a build concurrently
+    static constexpr int NSIDE = 6;
+    cudaStream_t side[NSIDE] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[NSIDE] = {};
     int4* d_coop_tasks = nullptr;
     bool coop_dirty = true;
 };
