@@ -75,6 +75,25 @@ int cq_basis_create(int natom, const double* xyz, const int* Z, int nshell,
                     const int* shell_nprim, const double* exps,
                     const double* coefs, cq_basis** out);
 
+/* cq_basis_create_batch: many independent molecules in one basis (batched
+ * execution of the Fock build and SCF).  atom_mol[natom] gives each atom's
+ * molecule, as consecutive ids 0,..,0,1,..,1,...; shells must be ordered by
+ * molecule.  Shell pairs and quartets are formed within a molecule only.
+ * Every matrix argument of the batched basis (densities, J, K, one-electron
+ * matrices, SCF densities) uses the batched layout: nmol slots of ld x ld
+ * (ld = the largest molecule's function count, cq_basis_layout), element
+ * (r, c) of molecule m at m*ld*ld + r*ld + c, padding elements zero.  A
+ * single-molecule basis has nmol = 1 and ld = nbf (the plain layout). */
+int cq_basis_create_batch(int natom, const double* xyz, const int* Z,
+                          const int* atom_mol, int nshell,
+                          const int* shell_atom, const int* shell_L,
+                          const int* shell_nprim, const double* exps,
+                          const double* coefs, cq_basis** out);
+
+/* Molecule count, slot dimension ld and functions per molecule (host
+ * array of nmol, may be NULL). */
+int cq_basis_layout(const cq_basis* b, int* nmol, int* ld, int* mol_n);
+
 /* Number of basis functions, shells, shell pairs. */
 int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npair);
 
@@ -83,7 +102,8 @@ void cq_basis_destroy(cq_basis* b);
 /* cq_schwarz: Schwarz factors Q_ab = sqrt(max_{m in a, n in b} |(mn|mn)|)
  * (screening of the direct build, Sec. "Reference Wave Functions": LinK-like
  * screening).  Q: device, nshell*nshell doubles (row-major, symmetric), or
- * NULL to only (re)compute the internal table.  Enqueued on `stream`. */
+ * NULL to only (re)compute the internal table (a batched basis accepts only
+ * NULL).  Enqueued on `stream`. */
 int cq_schwarz(cq_basis* b, double* Q, void* stream);
 
 typedef struct {
@@ -227,6 +247,21 @@ typedef struct {
 int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
            double* D_out, double* F_out, cq_scf_stats* stats, void* stream);
 
+/* Batched RHF SCF over the molecules of a batched basis
+ * (cq_basis_create_batch): one Fock build for all molecules per iteration,
+ * the dense steps as strided-batched GEMMs and a batched eigensolver on the
+ * ld x ld slots.  nocc: host array of nmol occupied-orbital counts.  D_in
+ * (device, batched layout, may be NULL for the core guess), D_out (device,
+ * batched layout), E_out and iters_out (host arrays of nmol, may be NULL).
+ * Options as for cq_scf (incremental builds are not used here).  Each
+ * molecule converges on its own (its density is then frozen); returns
+ * CQ_ERR_NOT_CONVERGED if any molecule reached max_iter.  stats->iterations
+ * is the number of batched iterations, stats->converged the number of
+ * converged molecules, stats->energy the sum of the energies. */
+int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opts,
+                 const double* D_in, double* D_out, double* E_out,
+                 int* iters_out, cq_scf_stats* stats, void* stream);
+
 /* One closed-shell RT-TDHF step of the Liouville-von Neumann equation (Eq.
  * lvn), in the orthonormal (Loewdin) basis:
  *   MMUT  P_{k+1} = U P_{k-1} U^+,  U = exp(-2 i dt F(P_k, t_k));
@@ -263,8 +298,10 @@ int cq_rt_step(cq_basis* b, const cq_rt_opts* opts, int step, void* P_prev,
  * eigenvectors; computes the one-electron data on first use. */
 int cq_dense_info(cq_basis* b, int* northo, int* ndropped, void* stream);
 
-/* Nuclear repulsion energy of the basis' nuclei (host result). */
+/* Nuclear repulsion energy of the basis' nuclei (host result; summed over
+ * the molecules of a batched basis), and per molecule (host array of nmol). */
 int cq_nuclear_repulsion(const cq_basis* b, double* E);
+int cq_nuclear_repulsion_batch(const cq_basis* b, double* E);
 
 const char* cq_last_error(void);
 

@@ -93,6 +93,11 @@ def lib():
         L.cq_rt_step.argtypes = [vp, ctypes.POINTER(RTOpts), ctypes.c_int, vp, vp, ctypes.POINTER(RTObs), vp]
         L.cq_dense_info.argtypes = [vp, ip, ip, vp]
         L.cq_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(FockOpts), ip, dp, vp]
+        L.cq_basis_create_batch.argtypes = [ctypes.c_int, dp, ip, ip, ctypes.c_int, ip, ip, ip, dp, dp,
+                                            ctypes.POINTER(vp)]
+        L.cq_basis_layout.argtypes = [vp, ip, ip, ip]
+        L.cq_scf_batch.argtypes = [vp, ip, ctypes.POINTER(SCFOpts), vp, vp, dp, ip, ctypes.POINTER(SCFStats), vp]
+        L.cq_nuclear_repulsion_batch.argtypes = [vp, dp]
         L.cq_fock_set_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_get_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
@@ -130,9 +135,13 @@ def peak_fma(fp32: bool, iters: int = 20000, stream=None) -> float:
 
 
 class Basis:
-    """A contracted Cartesian Gaussian basis on the current CUDA device."""
+    """A contracted Cartesian Gaussian basis on the current CUDA device.
 
-    def __init__(self, mol, basis):
+    Basis(mol, basis) holds one molecule; Basis.batch([(mol, basis), ...])
+    holds many independent molecules whose matrices use the batched layout
+    (nmol slots of ld x ld)."""
+
+    def __init__(self, mol, basis, atom_mol=None):
         L = lib()
         self.mol, self.basis = mol, basis
         xyz = np.ascontiguousarray(mol.xyz, dtype=np.float64)
@@ -144,14 +153,82 @@ class Basis:
         co = np.ascontiguousarray(basis.coefs, dtype=np.float64)
         dp, ip = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
         h = ctypes.c_void_p()
-        check(L.cq_basis_create(int(Z.shape[0]), xyz.ctypes.data_as(dp), Z.ctypes.data_as(ip),
-                                int(sl.shape[0]), sa.ctypes.data_as(ip), sl.ctypes.data_as(ip),
-                                sn.ctypes.data_as(ip), ex.ctypes.data_as(dp), co.ctypes.data_as(dp),
-                                ctypes.byref(h)), "cq_basis_create")
+        if atom_mol is None:
+            check(L.cq_basis_create(int(Z.shape[0]), xyz.ctypes.data_as(dp), Z.ctypes.data_as(ip),
+                                    int(sl.shape[0]), sa.ctypes.data_as(ip), sl.ctypes.data_as(ip),
+                                    sn.ctypes.data_as(ip), ex.ctypes.data_as(dp), co.ctypes.data_as(dp),
+                                    ctypes.byref(h)), "cq_basis_create")
+        else:
+            am = np.ascontiguousarray(atom_mol, dtype=np.int32)
+            check(L.cq_basis_create_batch(int(Z.shape[0]), xyz.ctypes.data_as(dp), Z.ctypes.data_as(ip),
+                                          am.ctypes.data_as(ip), int(sl.shape[0]), sa.ctypes.data_as(ip),
+                                          sl.ctypes.data_as(ip), sn.ctypes.data_as(ip),
+                                          ex.ctypes.data_as(dp), co.ctypes.data_as(dp), ctypes.byref(h)),
+                  "cq_basis_create_batch")
         self.h = h
         n, ns, npair = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         check(L.cq_basis_info(h, ctypes.byref(n), ctypes.byref(ns), ctypes.byref(npair)))
         self.nbf, self.nshell, self.npair = n.value, ns.value, npair.value
+        nm, ld = ctypes.c_int(), ctypes.c_int()
+        check(L.cq_basis_layout(h, ctypes.byref(nm), ctypes.byref(ld), None))
+        self.nmol, self.ld = nm.value, ld.value
+        mn = (ctypes.c_int * self.nmol)()
+        check(L.cq_basis_layout(h, None, None, mn))
+        self.mol_n = list(mn)
+
+    @classmethod
+    def batch(cls, items):
+        """One batched basis from a list of (Molecule, Basis) pairs."""
+        import synth
+        Zs, xyzs, am = [], [], []
+        sa, sl, sn, ex, co = [], [], [], [], []
+        aoff = 0
+        for m, (mol, bas) in enumerate(items):
+            Zs.append(mol.Z); xyzs.append(mol.xyz); am.append(np.full(mol.natom, m))
+            sa.append(bas.shell_atom + aoff); sl.append(bas.shell_L); sn.append(bas.shell_nprim)
+            ex.append(bas.exps); co.append(bas.coefs)
+            aoff += mol.natom
+        mol = synth.Molecule(np.concatenate(Zs).astype(np.int32), np.concatenate(xyzs))
+        bas = synth.Basis(np.concatenate(sa).astype(np.int32), np.concatenate(sl).astype(np.int32),
+                          np.concatenate(sn).astype(np.int32), np.concatenate(ex), np.concatenate(co))
+        out = cls(mol, bas, atom_mol=np.concatenate(am))
+        out.items = items
+        return out
+
+    def pack(self, mats):
+        """List of per-molecule (n_m, n_m[, ...]) arrays -> batched-layout tensor."""
+        import torch
+        first = torch.as_tensor(mats[0])
+        out = torch.zeros((self.nmol, self.ld, self.ld), dtype=first.dtype)
+        for m, M in enumerate(mats):
+            n = self.mol_n[m]
+            out[m, :n, :n] = torch.as_tensor(M)
+        return out.cuda()
+
+    def unpack(self, T):
+        """Batched-layout tensor -> list of per-molecule numpy arrays."""
+        T = T.reshape(self.nmol, self.ld, self.ld).cpu().numpy()
+        return [T[m, :self.mol_n[m], :self.mol_n[m]].copy() for m in range(self.nmol)]
+
+    def scf_batch(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
+                  mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, D0=None, stream=None,
+                  raise_on_fail=True):
+        """Batched RHF; returns (D batched tensor, energies, iterations, stats)."""
+        import torch
+        D = torch.empty((self.nmol, self.ld, self.ld), dtype=torch.float64, device="cuda")
+        no = np.ascontiguousarray(nocc, dtype=np.int32)
+        E = np.zeros(self.nmol)
+        it = np.zeros(self.nmol, dtype=np.int32)
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol)
+        st = SCFStats()
+        ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
+        rc = lib().cq_scf_batch(self.h, no.ctypes.data_as(ip), ctypes.byref(o),
+                                _ptr(D0) if D0 is not None else None, _ptr(D), E.ctypes.data_as(dp),
+                                it.ctypes.data_as(ip), ctypes.byref(st), _stream_ptr(stream))
+        if raise_on_fail:
+            check(rc, "cq_scf_batch")
+        return D, E, it, {"iterations": st.iterations, "converged": st.converged, "ms": st.ms,
+                          "quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32, "rc": rc}
 
     def close(self):
         if getattr(self, "h", None):
@@ -181,24 +258,25 @@ class Basis:
         float64 (n, n) real symmetric; complex128 (n, n) Hermitian;
         complex128 (4, n, n) Pauli components P^0..P^3."""
         import torch
-        n = self.nbf
+        n = self.ld
         if kind is None:
             if P.dtype == torch.float64:
                 kind = CQ_DENS_REAL_SYM
-            elif P.dim() == 3:
+            elif P.dim() == 3 and self.nmol == 1 or P.dim() == 4:
                 kind = CQ_DENS_PAULI4
             else:
                 kind = CQ_DENS_COMPLEX_HERM
         P = P.contiguous()
+        shape = (n, n) if self.nmol == 1 else (self.nmol, n, n)
         if want_J and J is None:
-            J = torch.empty((n, n), dtype=torch.float64, device=P.device)
+            J = torch.empty(shape, dtype=torch.float64, device=P.device)
         if want_K and K is None:
             if kind == CQ_DENS_REAL_SYM:
-                K = torch.empty((n, n), dtype=torch.float64, device=P.device)
+                K = torch.empty(shape, dtype=torch.float64, device=P.device)
             elif kind == CQ_DENS_COMPLEX_HERM:
-                K = torch.empty((n, n), dtype=torch.complex128, device=P.device)
+                K = torch.empty(shape, dtype=torch.complex128, device=P.device)
             else:
-                K = torch.empty((4, n, n), dtype=torch.complex128, device=P.device)
+                K = torch.empty((4,) + shape, dtype=torch.complex128, device=P.device)
         o = FockOpts(schwarz_tol, mixed_tol, prec, int(want_J), int(want_K))
         st = FockStats()
         check(lib().cq_fock_build(self.h, kind, _ptr(P), _ptr(J) if want_J else None,
@@ -231,9 +309,10 @@ class Basis:
     def one_electron(self, origin=(0.0, 0.0, 0.0), stream=None):
         """S, T, V (nbf x nbf) and dipole moment integrals M (3, nbf, nbf)."""
         import torch
-        n = self.nbf
-        S, T, V = (torch.empty((n, n), dtype=torch.float64, device="cuda") for _ in range(3))
-        M = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+        n = self.ld
+        shape = (n, n) if self.nmol == 1 else (self.nmol, n, n)
+        S, T, V = (torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(3))
+        M = torch.empty((3,) + shape, dtype=torch.float64, device="cuda")
         o = (ctypes.c_double * 3)(*origin)
         check(lib().cq_one_electron(self.h, _ptr(S), _ptr(T), _ptr(V), _ptr(M), o, _stream_ptr(stream)),
               "cq_one_electron")

@@ -154,7 +154,8 @@ static void free_basis(cq_basis* b)
                     b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
                     b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,
                     b->d_Kp, b->d_Dmax, b->d_cnt, b->d_coop_tasks, b->d_qlist, b->d_qcount,
-                    b->d_task_off, b->d_qoff, b->d_tcount, b->d_toff};
+                    b->d_task_off, b->d_qoff, b->d_tcount, b->d_toff, b->d_mol_n, b->d_mol_bfo,
+                    b->d_mol_nsh, b->d_mol_sho, b->d_mol_atom_off};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (b->ev0) cudaEventDestroy(b->ev0);
@@ -180,11 +181,13 @@ static int upload(T** d, const std::vector<T>& h)
     return CQ_OK;
 }
 
-static int create_impl(int natom, const double* xyz, const int* Z, int nshell, const int* shell_atom,
-                       const int* shell_L, const int* shell_nprim, const double* exps,
+static int create_impl(int natom, const double* xyz, const int* Z, const int* atom_mol, int nshell,
+                       const int* shell_atom, const int* shell_L, const int* shell_nprim, const double* exps,
                        const double* coefs, cq_basis* b)
 {
     CQ_CUDA(cudaGetDevice(&b->device));
+    b->atom_mol.assign(natom, 0);
+    if (atom_mol) b->atom_mol.assign(atom_mol, atom_mol + natom);
     for (int q = 0; q < NQC; ++q) {
         b->variant[q][0] = DEFAULT_VARIANT[q][0];
         b->variant[q][1] = DEFAULT_VARIANT[q][1];
@@ -210,33 +213,70 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     b->exps.assign(exps, exps + np);
     b->coefs.assign(coefs, coefs + np);
 
-    // ---- shell pairs, grouped by class and sorted by primitive count
+    // ---- molecules: atoms, shells and functions of each are contiguous
+    {
+        b->mol_atom_off.assign(1, 0);
+        for (int a = 1; a < natom; ++a)
+            if (b->atom_mol[a] != b->atom_mol[a - 1]) b->mol_atom_off.push_back(a);
+        b->mol_atom_off.push_back(natom);
+        b->nmol = (int)b->mol_atom_off.size() - 1;
+        b->mol_sho.assign(b->nmol + 1, nshell);
+        for (int s = nshell - 1; s >= 0; --s) b->mol_sho[b->atom_mol[b->atom[s]]] = s;
+        for (int m = b->nmol - 1; m >= 0; --m)
+            if (b->mol_sho[m] > b->mol_sho[m + 1]) b->mol_sho[m] = b->mol_sho[m + 1];
+        b->mol_bfo.resize(b->nmol + 1);
+        b->mol_n.resize(b->nmol);
+        b->mol_nsh.resize(b->nmol);
+        b->ld = b->lds = 1;
+        for (int m = 0; m < b->nmol; ++m) {
+            b->mol_bfo[m] = b->bfo[b->mol_sho[m]];
+            b->mol_nsh[m] = b->mol_sho[m + 1] - b->mol_sho[m];
+            b->mol_n[m] = b->bfo[b->mol_sho[m + 1]] - b->mol_bfo[m];
+            b->ld = std::max(b->ld, b->mol_n[m]);
+            b->lds = std::max(b->lds, b->mol_nsh[m]);
+        }
+        b->mol_bfo[b->nmol] = nbf;
+        b->mstride = (long long)b->nmol * b->ld * b->ld;
+    }
+
+    // ---- shell pairs within each molecule, grouped by class, then molecule,
+    // then sorted by primitive count
     std::vector<double> ctr(3 * nshell);
     for (int s = 0; s < nshell; ++s)
         for (int x = 0; x < 3; ++x) ctr[3 * s + x] = xyz[3 * b->atom[s] + x];
-    std::vector<std::vector<PairHdr>> bycls(NPC);
-    for (int a = 0; a < nshell; ++a)
-        for (int c = 0; c <= a; ++c) {
-            int s1 = a, s2 = c;
-            if (b->L[s1] < b->L[s2]) std::swap(s1, s2);
-            PairHdr h;
-            h.a = s1; h.b = s2;
-            h.bfa = b->bfo[s1]; h.bfb = b->bfo[s2];
-            h.nprim = b->nprim[s1] * b->nprim[s2];
-            h.poff = 0;
-            for (int x = 0; x < 3; ++x) h.AB[x] = ctr[3 * s1 + x] - ctr[3 * s2 + x];
-            bycls[pc_of(b->L[s1], b->L[s2])].push_back(h);
-        }
+    const int nmol = b->nmol;
+    std::vector<std::vector<PairHdr>> bycls(NPC * nmol);
+    for (int m = 0; m < nmol; ++m)
+        for (int a = b->mol_sho[m]; a < b->mol_sho[m + 1]; ++a)
+            for (int c = b->mol_sho[m]; c <= a; ++c) {
+                int s1 = a, s2 = c;
+                if (b->L[s1] < b->L[s2]) std::swap(s1, s2);
+                PairHdr h;
+                h.a = s1; h.b = s2;
+                h.bfa = b->bfo[s1] - b->mol_bfo[m]; h.bfb = b->bfo[s2] - b->mol_bfo[m];
+                h.sa = s1 - b->mol_sho[m]; h.sb = s2 - b->mol_sho[m];
+                h.mbase = (long long)m * b->ld * b->ld;
+                h.smbase = (long long)m * b->lds * b->lds;
+                h.nprim = b->nprim[s1] * b->nprim[s2];
+                h.poff = 0;
+                for (int x = 0; x < 3; ++x) h.AB[x] = ctr[3 * s1 + x] - ctr[3 * s2 + x];
+                bycls[pc_of(b->L[s1], b->L[s2]) * nmol + m].push_back(h);
+            }
     b->pairs.clear();
+    b->molcls_off.assign(NPC * (nmol + 1), 0);
     for (int c = 0; c < NPC; ++c) {
-        auto& v = bycls[c];
-        std::stable_sort(v.begin(), v.end(), [](const PairHdr& x, const PairHdr& y) {
-            if (x.nprim != y.nprim) return x.nprim > y.nprim;
-            if (x.a != y.a) return x.a < y.a;
-            return x.b < y.b;
-        });
         b->cls_off[c] = (int)b->pairs.size();
-        b->pairs.insert(b->pairs.end(), v.begin(), v.end());
+        for (int m = 0; m < nmol; ++m) {
+            auto& v = bycls[c * nmol + m];
+            std::stable_sort(v.begin(), v.end(), [](const PairHdr& x, const PairHdr& y) {
+                if (x.nprim != y.nprim) return x.nprim > y.nprim;
+                if (x.a != y.a) return x.a < y.a;
+                return x.b < y.b;
+            });
+            b->molcls_off[c * (nmol + 1) + m] = (int)b->pairs.size();
+            b->pairs.insert(b->pairs.end(), v.begin(), v.end());
+        }
+        b->molcls_off[c * (nmol + 1) + nmol] = (int)b->pairs.size();
     }
     b->cls_off[NPC] = (int)b->pairs.size();
     b->npair = (int)b->pairs.size();
@@ -244,27 +284,36 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     for (auto& h : b->pairs) { h.poff = q; q += h.nprim; }
     b->nprim_pairs = q;
 
-    // ---- warp tasks per quartet class: (bra, ket candidates [j0, j1)),
-    // costliest first.  The candidate range per task shrinks for classes
-    // with few quartets so that every class offers enough warps to fill the
-    // GPU (about 32 per SM).
+    // ---- warp tasks per quartet class: (bra, ket candidates [j0, j1)) with
+    // bra and kets of one molecule, costliest first.  The candidate range
+    // per task shrinks for classes with few quartets so that every class
+    // offers enough warps to fill the GPU (about 32 per SM).
     b->task_off.assign(NQC + 1, 0);
+    b->qoff.assign(NQC + 1, 0);
     std::vector<int4> tasks;
     for (int X = 0, qc = 0; X < NPC; ++X)
         for (int Y = 0; Y <= X; ++Y, ++qc) {
             b->task_off[qc] = (int)tasks.size();
-            const long nbra = b->cls_off[X + 1] - b->cls_off[X], nket = b->cls_off[Y + 1] - b->cls_off[Y];
-            const long cand = (X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket;
-            int range = (int)std::min<long>(JK_RANGE, std::max<long>(4, cand / (152 * 32)));
+            long long cand = 0;
+            for (int m = 0; m < nmol; ++m) {
+                const long long nbra = b->mol_range(X, m).second - b->mol_range(X, m).first;
+                const long long nket = b->mol_range(Y, m).second - b->mol_range(Y, m).first;
+                cand += (X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket;
+            }
+            b->qoff[qc + 1] = b->qoff[qc] + cand;
+            int range = (int)std::min<long long>(JK_RANGE, std::max<long long>(4, cand / (152 * 32)));
             range = std::max(4, range & ~3);
             std::vector<std::pair<double, int4>> tv;
-            for (int i = b->cls_off[X]; i < b->cls_off[X + 1]; ++i) {
-                const int jb = b->cls_off[Y], je = (X == Y) ? i + 1 : b->cls_off[Y + 1];
-                for (int j0 = jb; j0 < je; j0 += range) {
-                    const int j1 = std::min(je, j0 + range);
-                    double cost = 0.0;
-                    for (int j = j0; j < j1; ++j) cost += b->pairs[j].nprim;
-                    tv.push_back({cost * b->pairs[i].nprim, make_int4(i, j0, j1, 0)});
+            for (int m = 0; m < nmol; ++m) {
+                const auto br = b->mol_range(X, m), kr = b->mol_range(Y, m);
+                for (int i = br.first; i < br.second; ++i) {
+                    const int jb = kr.first, je = (X == Y) ? i + 1 : kr.second;
+                    for (int j0 = jb; j0 < je; j0 += range) {
+                        const int j1 = std::min(je, j0 + range);
+                        double cost = 0.0;
+                        for (int j = j0; j < j1; ++j) cost += b->pairs[j].nprim;
+                        tv.push_back({cost * b->pairs[i].nprim, make_int4(i, j0, j1, 0)});
+                    }
                 }
             }
             std::stable_sort(tv.begin(), tv.end(),
@@ -274,13 +323,6 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
             for (auto& t : tv) tasks.push_back(t.second);
         }
     b->task_off[NQC] = (int)tasks.size();
-    // list regions: one slot per candidate quartet of each class
-    b->qoff.assign(NQC + 1, 0);
-    for (int X = 0, qc = 0; X < NPC; ++X)
-        for (int Y = 0; Y <= X; ++Y, ++qc) {
-            const long long nbra = b->cls_off[X + 1] - b->cls_off[X], nket = b->cls_off[Y + 1] - b->cls_off[Y];
-            b->qoff[qc + 1] = b->qoff[qc] + ((X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket);
-        }
 
     // ---- device copies
     int rc;
@@ -300,6 +342,11 @@ static int create_impl(int natom, const double* xyz, const int* Z, int nshell, c
     if ((rc = dalloc(&b->d_tcount, 2 * tasks.size()))) return rc;
     if ((rc = dalloc(&b->d_toff, 2 * tasks.size()))) return rc;
     if ((rc = upload(&b->d_axyz, axyz))) return rc;
+    if ((rc = upload(&b->d_mol_n, b->mol_n))) return rc;
+    if ((rc = upload(&b->d_mol_bfo, b->mol_bfo))) return rc;
+    if ((rc = upload(&b->d_mol_nsh, b->mol_nsh))) return rc;
+    if ((rc = upload(&b->d_mol_sho, b->mol_sho))) return rc;
+    if ((rc = upload(&b->d_mol_atom_off, b->mol_atom_off))) return rc;
     if ((rc = upload(&b->d_Z, zc))) return rc;
     if ((rc = dalloc(&b->d_coef, np))) return rc;
     if ((rc = dalloc(&b->d_scale, nbf))) return rc;
@@ -355,8 +402,9 @@ int ensure_coop_tasks(cq_basis* b)
             b->coop_off[qc] = (int)tasks.size();
             if (b->variant[qc][0] != VARIANT_COOP && b->variant[qc][1] != VARIANT_COOP) continue;
             std::vector<std::pair<int, int4>> tv;
-            for (int i = b->cls_off[X]; i < b->cls_off[X + 1]; ++i) {
-                const int jb = b->cls_off[Y], je = (X == Y) ? i + 1 : b->cls_off[Y + 1];
+            for (int m = 0; m < b->nmol; ++m)
+            for (int i = b->mol_range(X, m).first; i < b->mol_range(X, m).second; ++i) {
+                const int jb = b->mol_range(Y, m).first, je = (X == Y) ? i + 1 : b->mol_range(Y, m).second;
                 for (int j = jb; j < je; ++j) {
                     const int np = b->pairs[i].nprim * b->pairs[j].nprim;
                     for (int p0 = 0; p0 < np; p0 += COOP_CHUNK) {
@@ -382,9 +430,41 @@ int ensure_coop_tasks(cq_basis* b)
 }
 }  // namespace cq
 
+static int create_checked(int natom, const double* xyz, const int* Z, const int* atom_mol, int nshell,
+                          const int* shell_atom, const int* shell_L, const int* shell_nprim, const double* exps,
+                          const double* coefs, cq_basis** out);
+
 extern "C" int cq_basis_create(int natom, const double* xyz, const int* Z, int nshell,
                                const int* shell_atom, const int* shell_L, const int* shell_nprim,
                                const double* exps, const double* coefs, cq_basis** out)
+{
+    return create_checked(natom, xyz, Z, nullptr, nshell, shell_atom, shell_L, shell_nprim, exps, coefs, out);
+}
+
+extern "C" int cq_basis_create_batch(int natom, const double* xyz, const int* Z, const int* atom_mol, int nshell,
+                                     const int* shell_atom, const int* shell_L, const int* shell_nprim,
+                                     const double* exps, const double* coefs, cq_basis** out)
+{
+    if (!atom_mol) { set_error("cq_basis_create_batch: atom_mol is NULL"); return CQ_ERR_INVALID_ARG; }
+    for (int a = 0; a < natom; ++a) {
+        if (atom_mol[a] < 0 || (a > 0 && atom_mol[a] != atom_mol[a - 1] && atom_mol[a] != atom_mol[a - 1] + 1) ||
+            (a == 0 && atom_mol[0] != 0)) {
+            set_error("cq_basis_create_batch: atom_mol must be 0,..,0,1,..,1,... (consecutive molecule ids)");
+            return CQ_ERR_INVALID_ARG;
+        }
+    }
+    for (int s = 1; s < nshell; ++s)
+        if (shell_atom && shell_atom[s] >= 0 && shell_atom[s] < natom && shell_atom[s - 1] >= 0 &&
+            shell_atom[s - 1] < natom && atom_mol[shell_atom[s]] < atom_mol[shell_atom[s - 1]]) {
+            set_error("cq_basis_create_batch: shells must be ordered by molecule");
+            return CQ_ERR_INVALID_ARG;
+        }
+    return create_checked(natom, xyz, Z, atom_mol, nshell, shell_atom, shell_L, shell_nprim, exps, coefs, out);
+}
+
+static int create_checked(int natom, const double* xyz, const int* Z, const int* atom_mol, int nshell,
+                          const int* shell_atom, const int* shell_L, const int* shell_nprim, const double* exps,
+                          const double* coefs, cq_basis** out)
 {
     if (!out) { set_error("cq_basis_create: out is NULL"); return CQ_ERR_INVALID_ARG; }
     *out = nullptr;
@@ -420,7 +500,7 @@ extern "C" int cq_basis_create(int natom, const double* xyz, const int* Z, int n
             return CQ_ERR_INVALID_ARG;
         }
     cq_basis* b = new cq_basis();
-    int rc = create_impl(natom, xyz, Z, nshell, shell_atom, shell_L, shell_nprim, exps, coefs, b);
+    int rc = create_impl(natom, xyz, Z, atom_mol, nshell, shell_atom, shell_L, shell_nprim, exps, coefs, b);
     if (rc) { free_basis(b); return rc; }
     *out = b;
     return CQ_OK;
@@ -430,6 +510,16 @@ extern "C" void cq_basis_destroy(cq_basis* b)
 {
     if (b) cudaDeviceSynchronize();
     free_basis(b);
+}
+
+extern "C" int cq_basis_layout(const cq_basis* b, int* nmol, int* ld, int* mol_n)
+{
+    if (!b) { set_error("cq_basis_layout: NULL basis"); return CQ_ERR_INVALID_ARG; }
+    if (nmol) *nmol = b->nmol;
+    if (ld) *ld = b->ld;
+    if (mol_n)
+        for (int m = 0; m < b->nmol; ++m) mol_n[m] = b->mol_n[m];
+    return CQ_OK;
 }
 
 extern "C" int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npair)
@@ -463,6 +553,10 @@ extern "C" int cq_schwarz(cq_basis* b, double* Q, void* stream)
         if (end > beg) SCHWARZ_LAUNCH[c](a, beg, end, b->d_Qf, b->d_Qd, s);
     }
     CQ_CUDA(cudaGetLastError());
+    if (Q && b->nmol > 1) {
+        set_error("cq_schwarz: the nshell x nshell table is only available for a single-molecule basis");
+        return CQ_ERR_UNSUPPORTED;
+    }
     if (Q) {
         schwarz_square_kernel<<<(b->npair + 127) / 128, 128, 0, s>>>(b->npair, b->d_pairs, b->d_Qd, b->nsh, Q);
         CQ_CUDA(cudaGetLastError());
@@ -470,16 +564,30 @@ extern "C" int cq_schwarz(cq_basis* b, double* Q, void* stream)
     return CQ_OK;
 }
 
+extern "C" int cq_nuclear_repulsion_batch(const cq_basis* b, double* E)
+{
+    if (!b || !E) { set_error("cq_nuclear_repulsion: NULL argument"); return CQ_ERR_INVALID_ARG; }
+    for (int m = 0; m < b->nmol; ++m) {
+        double e = 0.0;
+        for (int i = b->mol_atom_off[m]; i < b->mol_atom_off[m + 1]; ++i)
+            for (int j = b->mol_atom_off[m]; j < i; ++j) {
+                const double dx = b->xyz[3 * i] - b->xyz[3 * j], dy = b->xyz[3 * i + 1] - b->xyz[3 * j + 1],
+                             dz = b->xyz[3 * i + 2] - b->xyz[3 * j + 2];
+                e += (double)b->Z[i] * b->Z[j] / std::sqrt(dx * dx + dy * dy + dz * dz);
+            }
+        E[m] = e;
+    }
+    return CQ_OK;
+}
+
 extern "C" int cq_nuclear_repulsion(const cq_basis* b, double* E)
 {
     if (!b || !E) { set_error("cq_nuclear_repulsion: NULL argument"); return CQ_ERR_INVALID_ARG; }
-    double e = 0.0;
-    for (int i = 0; i < b->natom; ++i)
-        for (int j = 0; j < i; ++j) {
-            const double dx = b->xyz[3 * i] - b->xyz[3 * j], dy = b->xyz[3 * i + 1] - b->xyz[3 * j + 1],
-                         dz = b->xyz[3 * i + 2] - b->xyz[3 * j + 2];
-            e += (double)b->Z[i] * b->Z[j] / std::sqrt(dx * dx + dy * dy + dz * dz);
-        }
-    *E = e;
+    std::vector<double> e(b->nmol);
+    int rc = cq_nuclear_repulsion_batch(b, e.data());
+    if (rc) return rc;
+    double t = 0.0;
+    for (double x : e) t += x;
+    *E = t;
     return CQ_OK;
 }

@@ -25,10 +25,13 @@ using PrimPairF = PrimPairT<float>;
 // Contracted shell pair header.
 struct PairHdr {
     int a, b;        // shell indices (L[a] >= L[b])
-    int bfa, bfb;    // first basis function of a and b
+    int bfa, bfb;    // first basis function of a and b within their molecule
     int nprim;       // number of primitive pairs
     int poff;        // offset into the primitive-pair arrays
     double AB[3];    // A - B
+    int sa, sb;      // shell indices within the molecule
+    long long mbase; // offset of the molecule's matrix slot (elements)
+    long long smbase;// offset of the molecule's shell-block slot (density maxima)
 };
 
 // Per primitive quartet quantities consumed by the generated recurrences.

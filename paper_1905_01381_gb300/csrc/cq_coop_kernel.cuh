@@ -62,9 +62,10 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
     {
         const float* Dm = a.Dmax;
         const int ns = a.nsh;
-        float m = fmaxf(__ldg(Dm + B.a * ns + B.b), __ldg(Dm + K.a * ns + K.b));
-        m = fmaxf(m, fmaxf(__ldg(Dm + B.a * ns + K.a), __ldg(Dm + B.a * ns + K.b)));
-        m = fmaxf(m, fmaxf(__ldg(Dm + B.b * ns + K.a), __ldg(Dm + B.b * ns + K.b)));
+        const float* Ds = Dm + B.smbase;
+        float m = fmaxf(__ldg(Ds + B.sa * ns + B.sb), __ldg(Ds + K.sa * ns + K.sb));
+        m = fmaxf(m, fmaxf(__ldg(Ds + B.sa * ns + K.sa), __ldg(Ds + B.sa * ns + K.sb)));
+        m = fmaxf(m, fmaxf(__ldg(Ds + B.sb * ns + K.sa), __ldg(Ds + B.sb * ns + K.sb)));
         const float bound = __ldg(a.Q + ib) * __ldg(a.Q + j) * m;
         bool sel = bound >= a.tau;
         if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
@@ -173,12 +174,13 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
         if (K.a == K.b) sdeg *= R(0.5);
         if (j == ib) sdeg *= R(0.5);
         const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+        const long long mb = B.mbase;
         const int nJ = (a.want_j ? NA * NB + NC * ND : 0);
         const int nK = (a.want_k ? NA * NC + NA * ND + NB * NC + NB * ND : 0);
         for (int q = 0; q < a.nk; ++q) {
             if (q > 0 && !a.want_k) break;
-            const double* Dq = a.D + (size_t)q * n * n;
-            double* Kq = a.K + (size_t)q * n * n;
+            const double* Dq = a.D + (size_t)q * a.mstride;
+            double* Kq = a.K + (size_t)q * a.mstride;
             // density blocks: ab, cd, bd, bc, ad, ac (each <= 36)
             for (int e = lane; e < 216; e += 32) {
                 const int blk = e / 36, r = e - blk * 36;
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                     case 4: nr = NA; ncol = ND; rr = fa; cc = fd; break;
                     default: nr = NA; ncol = NC; rr = fa; cc = fc; break;
                 }
-                if (r < nr * ncol) Db[e] = ldR<R>(Dq + (size_t)(rr + r / ncol) * n + cc + r % ncol);
+                if (r < nr * ncol) Db[e] = ldR<R>(Dq + mb + (size_t)(rr + r / ncol) * n + cc + r % ncol);
             }
             __syncwarp();
             const int nout = (q == 0 ? nJ : 0) + nK;
@@ -205,20 +207,20 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                 if (kind == 0 && oo < NA * NB) {            // J'_ab
                     const int m = oo / NB, k = oo % NB;
                     for (int ls = 0; ls < NC * ND; ++ls) sum = fma(V[(m * NB + k) * NC * ND + ls], Db[36 + ls], sum);
-                    dst = a.J + (size_t)(fa + m) * n + fb + k;
+                    dst = a.J + mb + (size_t)(fa + m) * n + fb + k;
                     f = 2.0 * (double)sdeg;
                 } else if (kind == 0) {                       // J'_cd
                     oo -= NA * NB;
                     const int l = oo / ND, s = oo % ND;
                     for (int mk = 0; mk < NA * NB; ++mk) sum = fma(V[mk * NC * ND + l * ND + s], Db[mk], sum);
-                    dst = a.J + (size_t)(fc + l) * n + fd + s;
+                    dst = a.J + mb + (size_t)(fc + l) * n + fd + s;
                     f = 2.0 * (double)sdeg;
                 } else if (oo < NA * NC) {                    // K'_ac += (ab|cd) D_bd
                     const int m = oo / NC, l = oo % NC;
                     for (int k = 0; k < NB; ++k)
                         for (int s = 0; s < ND; ++s)
                             sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[72 + k * ND + s], sum);
-                    dst = Kq + (size_t)(fa + m) * n + fc + l;
+                    dst = Kq + mb + (size_t)(fa + m) * n + fc + l;
                     f = (double)sdeg;
                 } else if (oo < NA * NC + NA * ND) {          // K'_ad += (ab|cd) D_bc
                     oo -= NA * NC;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                     for (int k = 0; k < NB; ++k)
                         for (int l = 0; l < NC; ++l)
                             sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[108 + k * NC + l], sum);
-                    dst = Kq + (size_t)(fa + m) * n + fd + s;
+                    dst = Kq + mb + (size_t)(fa + m) * n + fd + s;
                     f = (double)sdeg;
                 } else if (oo < NA * NC + NA * ND + NB * NC) {  // K'_bc += (ab|cd) D_ad
                     oo -= NA * NC + NA * ND;
@@ -234,7 +236,7 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                     for (int m = 0; m < NA; ++m)
                         for (int s = 0; s < ND; ++s)
                             sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[144 + m * ND + s], sum);
-                    dst = Kq + (size_t)(fb + k) * n + fc + l;
+                    dst = Kq + mb + (size_t)(fb + k) * n + fc + l;
                     f = (double)sdeg;
                 } else {                                       // K'_bd += (ab|cd) D_ac
                     oo -= NA * NC + NA * ND + NB * NC;
@@ -242,7 +244,7 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
                     for (int m = 0; m < NA; ++m)
                         for (int l = 0; l < NC; ++l)
                             sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[180 + m * NC + l], sum);
-                    dst = Kq + (size_t)(fb + k) * n + fd + s;
+                    dst = Kq + mb + (size_t)(fb + k) * n + fd + s;
                     f = (double)sdeg;
                 }
                 atomicAdd(dst, f * (double)sum);

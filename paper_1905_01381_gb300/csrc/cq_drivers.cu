@@ -354,6 +354,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
     cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5};
     if (opts) o = *opts;
     const int n = b->nbf;
+    if (b->nmol > 1) { set_error("cq_scf: batched basis; use cq_scf_batch"); return CQ_ERR_UNSUPPORTED; }
     if (nocc <= 0 || nocc > n) { set_error("cq_scf: nocc out of range"); return CQ_ERR_INVALID_ARG; }
     if (o.max_iter <= 0 || o.diis_size < 1 || o.diis_size > DIIS_MAX) {
         set_error("cq_scf: max_iter must be > 0 and diis_size in 1..8");
@@ -669,6 +670,7 @@ extern "C" int cq_rt_step(cq_basis* b, const cq_rt_opts* opts, int step, void* P
         return CQ_ERR_INVALID_ARG;
     }
     const cq_rt_opts o = *opts;
+    if (b->nmol > 1) { set_error("cq_rt_step: batched basis not supported"); return CQ_ERR_UNSUPPORTED; }
     if (!(o.dt > 0.0) || step < 0) { set_error("cq_rt_step: dt must be > 0 and step >= 0"); return CQ_ERR_INVALID_ARG; }
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ensure_dense(b, s);

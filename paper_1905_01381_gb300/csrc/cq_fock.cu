@@ -22,66 +22,83 @@
 
 namespace cq {
 
-// P (layout by kind) -> nk scaled real matrices.
-__global__ void density_prep_kernel(int kind, int n, const double* __restrict__ P,
+// Matrices are stored as one slot per molecule: element (r, c) of molecule
+// m at m*ld*ld + r*ld + c, ld = the largest molecule's function count (for a
+// single molecule ld = nbf and the layout is the plain row-major matrix).
+// P (layout by kind) -> nk scaled real matrices; padding elements -> 0.
+__global__ void density_prep_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
+                                    const int* __restrict__ mol_bfo, const double* __restrict__ P,
                                     const double* __restrict__ sc, double* __restrict__ Dp)
 {
-    const size_t nn = (size_t)n * n;
+    const size_t slot = (size_t)ld * ld, ms = slot * nmol;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    const int r = (int)(i / n), c = (int)(i % n);
-    const double f = sc[r] * sc[c];
+    if (i >= ms) return;
+    const int m = (int)(i / slot);
+    const int r = (int)((i / ld) % ld), c = (int)(i % ld);
+    const int nm = mol_n[m];
+    const double f = (r < nm && c < nm) ? sc[mol_bfo[m] + r] * sc[mol_bfo[m] + c] : 0.0;
     if (kind == CQ_DENS_REAL_SYM) {
         Dp[i] = f * P[i];
     } else if (kind == CQ_DENS_COMPLEX_HERM) {
         Dp[i] = f * P[2 * i];
-        Dp[nn + i] = f * P[2 * i + 1];
+        Dp[ms + i] = f * P[2 * i + 1];
     } else {
         for (int I = 0; I < 4; ++I) {
-            Dp[(2 * I) * nn + i] = f * P[2 * (I * nn + i)];
-            Dp[(2 * I + 1) * nn + i] = f * P[2 * (I * nn + i) + 1];
+            Dp[(2 * I) * ms + i] = f * P[2 * (I * ms + i)];
+            Dp[(2 * I + 1) * ms + i] = f * P[2 * (I * ms + i) + 1];
         }
     }
 }
 
-// Shell-block maxima of |P'| over all nk matrices.
-__global__ void dmax_kernel(int nsh, int n, int nk, const int* __restrict__ bfo, const double* __restrict__ Dp,
-                            float* __restrict__ Dmax)
+// Shell-block maxima of |P'| over all nk matrices, one slot of lds x lds
+// per molecule (lds = the largest molecule's shell count).
+__global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ mol_nsh, const int* __restrict__ mol_sho,
+                            const int* __restrict__ mol_bfo, const int* __restrict__ bfo, int nk,
+                            const double* __restrict__ Dp, float* __restrict__ Dmax)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nsh * nsh) return;
-    const int a = p / nsh, b = p % nsh;
-    double m = 0.0;
+    const size_t sslot = (size_t)lds * lds;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sslot * nmol) return;
+    const int m = (int)(p / sslot);
+    const int sa = (int)((p / lds) % lds), sb = (int)(p % lds);
+    if (sa >= mol_nsh[m] || sb >= mol_nsh[m]) { Dmax[p] = 0.f; return; }
+    const int a = mol_sho[m] + sa, b = mol_sho[m] + sb, f0 = mol_bfo[m];
+    const size_t slot = (size_t)ld * ld, ms = slot * nmol;
+    double mx = 0.0;
     for (int q = 0; q < nk; ++q)
         for (int i = bfo[a]; i < bfo[a + 1]; ++i)
-            for (int j = bfo[b]; j < bfo[b + 1]; ++j) m = fmax(m, fabs(Dp[(size_t)q * n * n + (size_t)i * n + j]));
-    Dmax[p] = (float)m * 1.0000005f;
+            for (int j = bfo[b]; j < bfo[b + 1]; ++j)
+                mx = fmax(mx, fabs(Dp[(size_t)q * ms + m * slot + (size_t)(i - f0) * ld + (j - f0)]));
+    Dmax[p] = (float)mx * 1.0000005f;
 }
 
-// J = s s (J' + J'^T); K_q = s s (K'_q +/- K'_q^T) written in the output layout.
-__global__ void finalize_kernel(int kind, int n, const double* __restrict__ sc, const double* __restrict__ Jp,
-                                const double* __restrict__ Kp, double* __restrict__ J, double* __restrict__ K,
-                                int want_j, int want_k)
+// J = s s (J' + J'^T); K_q = s s (K'_q +/- K'_q^T), per slot, in the output layout.
+__global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
+                                const int* __restrict__ mol_bfo, const double* __restrict__ sc,
+                                const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
+                                double* __restrict__ K, int want_j, int want_k)
 {
-    const size_t nn = (size_t)n * n;
+    const size_t slot = (size_t)ld * ld, ms = slot * nmol;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nn) return;
-    const int r = (int)(i / n), c = (int)(i % n);
-    const size_t t = (size_t)c * n + r;
-    const double f = sc[r] * sc[c];
+    if (i >= ms) return;
+    const int m = (int)(i / slot);
+    const int r = (int)((i / ld) % ld), c = (int)(i % ld);
+    const size_t t = (size_t)m * slot + (size_t)c * ld + r;
+    const int nm = mol_n[m];
+    const double f = (r < nm && c < nm) ? sc[mol_bfo[m] + r] * sc[mol_bfo[m] + c] : 0.0;
     if (want_j) J[i] = f * (Jp[i] + Jp[t]);
     if (!want_k) return;
     if (kind == CQ_DENS_REAL_SYM) {
         K[i] = f * (Kp[i] + Kp[t]);
     } else if (kind == CQ_DENS_COMPLEX_HERM) {
         K[2 * i] = f * (Kp[i] + Kp[t]);
-        K[2 * i + 1] = f * (Kp[nn + i] - Kp[nn + t]);
+        K[2 * i + 1] = f * (Kp[ms + i] - Kp[ms + t]);
     } else {
         for (int I = 0; I < 4; ++I) {
-            const double* Kr = Kp + (2 * I) * nn;
-            const double* Ki = Kp + (2 * I + 1) * nn;
-            K[2 * (I * nn + i)] = f * (Kr[i] + Kr[t]);
-            K[2 * (I * nn + i) + 1] = f * (Ki[i] - Ki[t]);
+            const double* Kr = Kp + (2 * I) * ms;
+            const double* Ki = Kp + (2 * I + 1) * ms;
+            K[2 * (I * ms + i)] = f * (Kr[i] + Kr[t]);
+            K[2 * (I * ms + i) + 1] = f * (Ki[i] - Ki[t]);
         }
     }
 }
@@ -100,7 +117,7 @@ static int nk_of(int kind) { return kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DE
 int ensure_scratch(cq_basis* b, int nk)
 {
     if (nk <= b->nk_cap) return CQ_OK;
-    const size_t nn = (size_t)b->nbf * b->nbf;
+    const size_t nn = b->mstride;
     if (b->d_Dp) cudaFree(b->d_Dp);
     if (b->d_Kp) cudaFree(b->d_Kp);
     b->d_Dp = b->d_Kp = nullptr;
@@ -108,7 +125,7 @@ int ensure_scratch(cq_basis* b, int nk)
     if ((rc = dalloc(&b->d_Dp, nn * nk))) return rc;
     if ((rc = dalloc(&b->d_Kp, nn * nk))) return rc;
     if (!b->d_Jp && (rc = dalloc(&b->d_Jp, nn))) return rc;
-    if (!b->d_Dmax && (rc = dalloc(&b->d_Dmax, (size_t)b->nsh * b->nsh))) return rc;
+    if (!b->d_Dmax && (rc = dalloc(&b->d_Dmax, (size_t)b->nmol * b->lds * b->lds))) return rc;
     b->nk_cap = nk;
     return CQ_OK;
 }
@@ -116,13 +133,12 @@ int ensure_scratch(cq_basis* b, int nk)
 // Screening and precision split of the candidates of one static task:
 // returns this lane's class of candidate j0 + lane (-1 rejected, 0 FP64,
 // 1 FP32).
-__device__ __forceinline__ int classify_one(const ClassifyArgs& c, int j, int jend, int ba, int bb, float Qb,
-                                            float dab)
+__device__ __forceinline__ int classify_one(const ClassifyArgs& c, const float* Dm, int j, int jend, int ba, int bb,
+                                            float Qb, float dab)
 {
     if (j >= jend) return -1;
-    const float* Dm = c.Dmax;
     const int ns = c.nsh;
-    const int kc = __ldg(&c.pairs[j].a), kd = __ldg(&c.pairs[j].b);
+    const int kc = __ldg(&c.pairs[j].sa), kd = __ldg(&c.pairs[j].sb);
     float m = fmaxf(dab, __ldg(Dm + kc * ns + kd));
     m = fmaxf(m, fmaxf(__ldg(Dm + ba * ns + kc), __ldg(Dm + ba * ns + kd)));
     m = fmaxf(m, fmaxf(__ldg(Dm + bb * ns + kc), __ldg(Dm + bb * ns + kd)));
@@ -147,15 +163,16 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
     while (qc + 1 < nqc && c.cls_task_off[qc + 1] <= w) ++qc;
     const int4 t = c.tasks[w];
     const int ib = t.x;
-    const int ba = __ldg(&c.pairs[ib].a), bb = __ldg(&c.pairs[ib].b);
+    const int ba = __ldg(&c.pairs[ib].sa), bb = __ldg(&c.pairs[ib].sb);
     const float Qb = __ldg(c.Q + ib);
-    const float dab = __ldg(c.Dmax + ba * c.nsh + bb);
+    const float* Dm = c.Dmax + __ldg(&c.pairs[ib].smbase);
+    const float dab = __ldg(Dm + ba * c.nsh + bb);
     const long long base = c.cls_qoff[qc], top = c.cls_qoff[qc + 1];
     unsigned int n0 = 0, n1 = 0;
     unsigned int o0 = write ? toff[2 * w] : 0, o1 = write ? toff[2 * w + 1] : 0;
     for (int j0 = t.y; j0 < t.z; j0 += 32) {
         const int j = j0 + lane;
-        const int prec = classify_one(c, j, t.z, ba, bb, Qb, dab);
+        const int prec = classify_one(c, Dm, j, t.z, ba, bb, Qb, dab);
         const unsigned m0 = __ballot_sync(0xffffffffu, prec == 0);
         const unsigned m1 = __ballot_sync(0xffffffffu, prec == 1);
         if (write) {
@@ -213,7 +230,7 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     ClassifyArgs c;
     c.pairs = b->d_pairs; c.tasks = b->d_tasks; c.ntasks = b->task_off[NQC];
     c.cls_task_off = b->d_task_off; c.cls_qoff = b->d_qoff;
-    c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->nsh;
+    c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->lds;
     c.tau = a.tau; c.tau_mixed = a.tau_mixed; c.split = o.prec == CQ_PREC_MIXED;
     c.qlist = b->d_qlist; c.qcount = b->d_qcount;
     if (c.ntasks > 0) {
@@ -341,12 +358,15 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     if (rc) return rc;
     if ((rc = ensure_coop_tasks(b))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    const int n = b->nbf;
-    const size_t nn = (size_t)n * n;
+    const int n = b->ld;
+    const size_t nn = b->mstride;
     const int nb = (int)((nn + 255) / 256);
     if (stats) CQ_CUDA(cudaEventRecord(b->ev0, s));
-    density_prep_kernel<<<nb, 256, 0, s>>>(kind, n, (const double*)P, b->d_scale, b->d_Dp);
-    dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, b->d_Dp, b->d_Dmax);
+    density_prep_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, (const double*)P, b->d_scale,
+                                           b->d_Dp);
+    const size_t nsl = (size_t)b->nmol * b->lds * b->lds;
+    dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
+                                                              b->d_mol_bfo, b->d_bfo, nk, b->d_Dp, b->d_Dmax);
     CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
@@ -354,7 +374,8 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
-    a.Q = b->d_Qf; a.Dmax = b->d_Dmax; a.nsh = b->nsh;
+    a.Q = b->d_Qf; a.Dmax = b->d_Dmax; a.nsh = b->lds;
+    a.mstride = (long long)nn;
     a.tau = (float)o.schwarz_tol;
     a.tau_mixed = (float)o.mixed_tol;
     a.D = b->d_Dp; a.nk = nk; a.nbf = n;
@@ -366,7 +387,8 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     if (rc) return rc;
     CQ_CUDA(cudaGetLastError());
     counter_total_kernel<<<1, 32, 0, s>>>(b->d_cnt);
-    finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, b->d_Jp, b->d_Kp, J, (double*)K, o.want_J, o.want_K);
+    finalize_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, b->d_scale, b->d_Jp, b->d_Kp, J,
+                                       (double*)K, o.want_J, o.want_K);
     CQ_CUDA(cudaGetLastError());
     if (stats) {
         CQ_CUDA(cudaEventRecord(b->ev1, s));
@@ -423,8 +445,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     if (!b || !P) { set_error("cq_autotune: NULL argument"); return CQ_ERR_INVALID_ARG; }
     cq_fock_opts o{1e-14, 1e-3, CQ_PREC_MIXED, 1, 1};
     if (opts) o = *opts;
-    const int n = b->nbf;
-    const size_t nn = (size_t)n * n;
+    const size_t nn = b->mstride;
     const int nk = nk_of(kind);
     double *J = nullptr, *K = nullptr;
     int rc;

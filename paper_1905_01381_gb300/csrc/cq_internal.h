@@ -56,6 +56,18 @@ int dalloc(T** p, size_t n)
 struct cq_basis {
     int device = 0;
     int natom = 0, nsh = 0, nbf = 0, npair = 0, nprim_pairs = 0;
+    // molecules of a batched basis (one molecule for cq_basis_create): every
+    // matrix is stored as nmol slots of ld x ld, shell blocks as lds x lds
+    int nmol = 1, ld = 0, lds = 0;
+    long long mstride = 0;
+    std::vector<int> atom_mol, mol_atom_off, mol_sho, mol_bfo, mol_n, mol_nsh;
+    std::vector<int> molcls_off;   // NPC x (nmol + 1) pair offsets per class and molecule
+    int *d_mol_n = nullptr, *d_mol_bfo = nullptr, *d_mol_nsh = nullptr, *d_mol_sho = nullptr,
+        *d_mol_atom_off = nullptr;
+    std::pair<int, int> mol_range(int c, int m) const
+    {
+        return {molcls_off[c * (nmol + 1) + m], molcls_off[c * (nmol + 1) + m + 1]};
+    }
     std::vector<double> xyz;
     std::vector<int> Z;
     std::vector<int> L, nprim, poff, atom, bfo;

@@ -25,7 +25,8 @@ struct JKArgs {
     int prec_sel;                 // 0: every surviving quartet; 1: bound >= tau_mixed; 2: bound < tau_mixed
     const double* D;              // nk scaled density matrices, nbf x nbf each
     int nk;
-    int nbf;
+    int nbf;                      // leading dimension of every matrix slot
+    long long mstride;            // elements of one matrix over all slots (density q at q * mstride)
     int want_j, want_k;
     double* J;                    // J' accumulator nbf x nbf
     double* K;                    // K' accumulators nk x nbf x nbf
@@ -136,18 +137,19 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     const int n = a.nbf;
     const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+    const long long mb = B.mbase;
     if (a.want_j) {
         const double* D0 = a.D;
         R dab[NA * NB], dcd[NC * ND], jcd[NC * ND];
 #pragma unroll
         for (int m = 0; m < NA; ++m)
 #pragma unroll
-            for (int k = 0; k < NB; ++k) dab[m * NB + k] = ldR<R>(D0 + (size_t)(fa + m) * n + fb + k);
+            for (int k = 0; k < NB; ++k) dab[m * NB + k] = ldR<R>(D0 + mb + (size_t)(fa + m) * n + fb + k);
 #pragma unroll
         for (int l = 0; l < NC; ++l)
 #pragma unroll
             for (int s = 0; s < ND; ++s) {
-                dcd[l * ND + s] = ldR<R>(D0 + (size_t)(fc + l) * n + fd + s);
+                dcd[l * ND + s] = ldR<R>(D0 + mb + (size_t)(fc + l) * n + fd + s);
                 jcd[l * ND + s] = R(0);
             }
 #pragma unroll
@@ -166,28 +168,28 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
         for (int l = 0; l < NC; ++l)
 #pragma unroll
             for (int s = 0; s < ND; ++s)
-                atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)jcd[l * ND + s]);
+                atomicAdd(a.J + mb + (size_t)(fc + l) * n + fd + s, f * (double)jcd[l * ND + s]);
     }
     if (a.want_k) {
 #pragma unroll 1
         for (int q = 0; q < a.nk; ++q) {
-            const double* Dq = a.D + (size_t)q * n * n;
-            double* Kq = a.K + (size_t)q * n * n;
+            const double* Dq = a.D + (size_t)q * a.mstride;
+            double* Kq = a.K + (size_t)q * a.mstride;
             R dbd[NB * ND], dbc[NB * NC], dad[NA * ND], dac[NA * NC];
             R kac[NA * NC], kad[NA * ND], kbc[NB * NC], kbd[NB * ND];
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
 #pragma unroll
-                for (int s = 0; s < ND; ++s) { dbd[k * ND + s] = ldR<R>(Dq + (size_t)(fb + k) * n + fd + s); kbd[k * ND + s] = R(0); }
+                for (int s = 0; s < ND; ++s) { dbd[k * ND + s] = ldR<R>(Dq + mb + (size_t)(fb + k) * n + fd + s); kbd[k * ND + s] = R(0); }
 #pragma unroll
-                for (int l = 0; l < NC; ++l) { dbc[k * NC + l] = ldR<R>(Dq + (size_t)(fb + k) * n + fc + l); kbc[k * NC + l] = R(0); }
+                for (int l = 0; l < NC; ++l) { dbc[k * NC + l] = ldR<R>(Dq + mb + (size_t)(fb + k) * n + fc + l); kbc[k * NC + l] = R(0); }
             }
 #pragma unroll
             for (int m = 0; m < NA; ++m) {
 #pragma unroll
-                for (int s = 0; s < ND; ++s) { dad[m * ND + s] = ldR<R>(Dq + (size_t)(fa + m) * n + fd + s); kad[m * ND + s] = R(0); }
+                for (int s = 0; s < ND; ++s) { dad[m * ND + s] = ldR<R>(Dq + mb + (size_t)(fa + m) * n + fd + s); kad[m * ND + s] = R(0); }
 #pragma unroll
-                for (int l = 0; l < NC; ++l) { dac[m * NC + l] = ldR<R>(Dq + (size_t)(fa + m) * n + fc + l); kac[m * NC + l] = R(0); }
+                for (int l = 0; l < NC; ++l) { dac[m * NC + l] = ldR<R>(Dq + mb + (size_t)(fa + m) * n + fc + l); kac[m * NC + l] = R(0); }
             }
 #pragma unroll
             for (int m = 0; m < NA; ++m)
@@ -207,16 +209,16 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
 #pragma unroll
             for (int m = 0; m < NA; ++m) {
 #pragma unroll
-                for (int l = 0; l < NC; ++l) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)kac[m * NC + l]);
+                for (int l = 0; l < NC; ++l) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fc + l, f * (double)kac[m * NC + l]);
 #pragma unroll
-                for (int s = 0; s < ND; ++s) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)kad[m * ND + s]);
+                for (int s = 0; s < ND; ++s) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fd + s, f * (double)kad[m * ND + s]);
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
 #pragma unroll
-                for (int l = 0; l < NC; ++l) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)kbc[k * NC + l]);
+                for (int l = 0; l < NC; ++l) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fc + l, f * (double)kbc[k * NC + l]);
 #pragma unroll
-                for (int s = 0; s < ND; ++s) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)kbd[k * ND + s]);
+                for (int s = 0; s < ND; ++s) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fd + s, f * (double)kbd[k * ND + s]);
             }
         }
     }
@@ -238,17 +240,18 @@ __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, 
     R* kbd = kbc + NB * NC;
     const int n = a.nbf;
     const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
-    const double* Dq = a.D + (size_t)q * n * n;
+    const long long mb = B.mbase;
+    const double* Dq = a.D + (size_t)q * a.mstride;
     if (q == 0 && a.want_j) {
         R dcd[NCD];
 #pragma unroll
         for (int l = 0; l < NC; ++l)
 #pragma unroll
-            for (int s = 0; s < ND; ++s) dcd[l * ND + s] = ldR<R>(Dq + (size_t)(fc + l) * n + fd + s);
+            for (int s = 0; s < ND; ++s) dcd[l * ND + s] = ldR<R>(Dq + mb + (size_t)(fc + l) * n + fd + s);
 #pragma unroll 1
         for (int mn = sub; mn < NA * NB; mn += G) {
             const int m = mn / NB, k = mn - (mn / NB) * NB;
-            const R dab = ldR<R>(Dq + (size_t)(fa + m) * n + fb + k);
+            const R dab = ldR<R>(Dq + mb + (size_t)(fa + m) * n + fb + k);
             R t = R(0);
 #pragma unroll
             for (int ls = 0; ls < NCD; ++ls) {
@@ -256,7 +259,7 @@ __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, 
                 t = fma(v, dcd[ls], t);
                 jcd[ls] = fma(v, dab, jcd[ls]);
             }
-            atomicAdd(a.J + (size_t)(fa + m) * n + fb + k, 2.0 * (double)sdeg * (double)t);
+            atomicAdd(a.J + mb + (size_t)(fa + m) * n + fb + k, 2.0 * (double)sdeg * (double)t);
         }
     }
     if (a.want_k) {
@@ -266,13 +269,13 @@ __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, 
             R dbd[ND], dbc[NC], dad[ND], dac[NC];
 #pragma unroll
             for (int s = 0; s < ND; ++s) {
-                dbd[s] = ldR<R>(Dq + (size_t)(fb + k) * n + fd + s);
-                dad[s] = ldR<R>(Dq + (size_t)(fa + m) * n + fd + s);
+                dbd[s] = ldR<R>(Dq + mb + (size_t)(fb + k) * n + fd + s);
+                dad[s] = ldR<R>(Dq + mb + (size_t)(fa + m) * n + fd + s);
             }
 #pragma unroll
             for (int l = 0; l < NC; ++l) {
-                dbc[l] = ldR<R>(Dq + (size_t)(fb + k) * n + fc + l);
-                dac[l] = ldR<R>(Dq + (size_t)(fa + m) * n + fc + l);
+                dbc[l] = ldR<R>(Dq + mb + (size_t)(fb + k) * n + fc + l);
+                dac[l] = ldR<R>(Dq + mb + (size_t)(fa + m) * n + fc + l);
             }
 #pragma unroll
             for (int l = 0; l < NC; ++l)
@@ -397,7 +400,7 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
                     if (same[k]) v += u;
                 }
                 if (head && on && v != 0.0)
-                    atomicAdd(a.J + (size_t)(B.bfa + i / NB) * a.nbf + B.bfb + i % NB, v);
+                    atomicAdd(a.J + B.mbase + (size_t)(B.bfa + i / NB) * a.nbf + B.bfb + i % NB, v);
             }
         }
     } else {
@@ -409,6 +412,7 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
         }
         const int n = a.nbf;
         const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+    const long long mb = B.mbase;
 #pragma unroll 1
         for (int q = 0; q < a.nk; ++q) {
             if (q > 0 && !a.want_k) break;
@@ -426,11 +430,11 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
                     for (int s = 0; s < ND; ++s) {
                         const R v = group_sum<R, G>(jcd[l * ND + s]);
                         if (on && ((l * ND + s) % G) == sub)
-                            atomicAdd(a.J + (size_t)(fc + l) * n + fd + s, f * (double)v);
+                            atomicAdd(a.J + mb + (size_t)(fc + l) * n + fd + s, f * (double)v);
                     }
             }
             if (a.want_k) {
-                double* Kq = a.K + (size_t)q * n * n;
+                double* Kq = a.K + (size_t)q * a.mstride;
                 const double f = (double)sdeg;
                 int e2 = 0;
 #pragma unroll
@@ -438,28 +442,28 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
 #pragma unroll
                     for (int l = 0; l < NC; ++l, ++e2) {
                         const R v = group_sum<R, G>(kb[m * NC + l]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fc + l, f * (double)v);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fc + l, f * (double)v);
                     }
 #pragma unroll
                 for (int m = 0; m < NA; ++m)
 #pragma unroll
                     for (int s = 0; s < ND; ++s, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + m * ND + s]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fa + m) * n + fd + s, f * (double)v);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fd + s, f * (double)v);
                     }
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
 #pragma unroll
                     for (int l = 0; l < NC; ++l, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + NA * ND + k * NC + l]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fc + l, f * (double)v);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fc + l, f * (double)v);
                     }
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
 #pragma unroll
                     for (int s = 0; s < ND; ++s, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + NA * ND + NB * NC + k * ND + s]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + (size_t)(fb + k) * n + fd + s, f * (double)v);
+                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fd + s, f * (double)v);
                     }
             }
         }

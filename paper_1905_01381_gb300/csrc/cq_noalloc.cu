@@ -18,13 +18,16 @@
 namespace cq {
 
 // kernels of the ordinary build (cq_fock.cu), reused unchanged
-__global__ void density_prep_kernel(int kind, int n, const double* __restrict__ P, const double* __restrict__ sc,
-                                    double* __restrict__ Dp);
-__global__ void dmax_kernel(int nsh, int n, int nk, const int* __restrict__ bfo, const double* __restrict__ Dp,
-                            float* __restrict__ Dmax);
-__global__ void finalize_kernel(int kind, int n, const double* __restrict__ sc, const double* __restrict__ Jp,
-                                const double* __restrict__ Kp, double* __restrict__ J, double* __restrict__ K,
-                                int want_j, int want_k);
+__global__ void density_prep_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
+                                    const int* __restrict__ mol_bfo, const double* __restrict__ P,
+                                    const double* __restrict__ sc, double* __restrict__ Dp);
+__global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ mol_nsh, const int* __restrict__ mol_sho,
+                            const int* __restrict__ mol_bfo, const int* __restrict__ bfo, int nk,
+                            const double* __restrict__ Dp, float* __restrict__ Dmax);
+__global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
+                                const int* __restrict__ mol_bfo, const double* __restrict__ sc,
+                                const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
+                                double* __restrict__ K, int want_j, int want_k);
 
 // Scratch of the allocation-free build: 16 MiB held by every device that
 // loads the library, for as long as the library stays loaded.
@@ -70,6 +73,15 @@ extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
            round256((size_t)nshell * nshell * sizeof(float)) + round256((4 + 6 * NQC) * sizeof(unsigned long long));
 }
 
+static size_t noalloc_bytes(const cq_basis* b, int kind)
+{
+    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const size_t nn = b->mstride;
+    return round256(nn * nk * sizeof(double)) * 2 + round256(nn * sizeof(double)) +
+           round256((size_t)b->nmol * b->lds * b->lds * sizeof(float)) +
+           round256((4 + 6 * NQC) * sizeof(unsigned long long));
+}
+
 extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, double* J, void* K,
                                      const cq_fock_opts* opts, void* stream)
 {
@@ -89,7 +101,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
         set_error("cq_fock_build_noalloc: bad options");
         return CQ_ERR_INVALID_ARG;
     }
-    const size_t need = cq_fock_noalloc_scratch_bytes(kind, b->nbf, b->nsh);
+    const size_t need = noalloc_bytes(b, kind);
     if (need > NOALLOC_SCRATCH_BYTES) {
         set_error("cq_fock_build_noalloc: basis too large for the fixed 16 MiB scratch (needs " +
                   std::to_string(need) + " bytes); use cq_fock_build");
@@ -99,19 +111,21 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     int rc = scratch_address(&base);
     if (rc) return rc;
     const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
-    const int n = b->nbf;
-    const size_t nn = (size_t)n * n;
+    const int n = b->ld;
+    const size_t nn = b->mstride;
     unsigned char* p = (unsigned char*)base;
     double* Dp = (double*)p;          p += round256(nn * nk * sizeof(double));
     double* Kp = (double*)p;          p += round256(nn * nk * sizeof(double));
     double* Jp = (double*)p;          p += round256(nn * sizeof(double));
-    float* Dmax = (float*)p;          p += round256((size_t)b->nsh * b->nsh * sizeof(float));
+    float* Dmax = (float*)p;          p += round256((size_t)b->nmol * b->lds * b->lds * sizeof(float));
     unsigned long long* cnt = (unsigned long long*)p;
 
     cudaStream_t s = (cudaStream_t)stream;
     const int nb = (int)((nn + 255) / 256);
-    density_prep_kernel<<<nb, 256, 0, s>>>(kind, n, (const double*)P, b->d_scale, Dp);
-    dmax_kernel<<<(b->nsh * b->nsh + 127) / 128, 128, 0, s>>>(b->nsh, n, nk, b->d_bfo, Dp, Dmax);
+    density_prep_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, (const double*)P, b->d_scale, Dp);
+    const size_t nsl = (size_t)b->nmol * b->lds * b->lds;
+    dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
+                                                              b->d_mol_bfo, b->d_bfo, nk, Dp, Dmax);
     // the array keeps the previous call's contents: clear the accumulators
     CQ_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(Kp, 0, nn * nk * sizeof(double), s));
@@ -119,7 +133,8 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
-    a.Q = b->d_Qf; a.Dmax = Dmax; a.nsh = b->nsh;
+    a.Q = b->d_Qf; a.Dmax = Dmax; a.nsh = b->lds;
+    a.mstride = (long long)nn;
     a.tau = (float)o.schwarz_tol;
     a.tau_mixed = (float)o.mixed_tol;
     a.D = Dp; a.nk = nk; a.nbf = n;
@@ -130,7 +145,8 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     rc = classify_and_launch(b, a, o, false, s);
     if (rc) return rc;
     CQ_CUDA(cudaGetLastError());
-    finalize_kernel<<<nb, 256, 0, s>>>(kind, n, b->d_scale, Jp, Kp, J, (double*)K, o.want_J, o.want_K);
+    finalize_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, b->d_scale, Jp, Kp, J, (double*)K,
+                                       o.want_J, o.want_K);
     CQ_CUDA(cudaGetLastError());
     return CQ_OK;
 }

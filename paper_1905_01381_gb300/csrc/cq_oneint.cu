@@ -31,17 +31,28 @@ __device__ __forceinline__ void boys_rt(int L, double T, double* F, const double
 // index of a Cartesian exponent triple with total <= 4 in a 5x5x5 cube
 __device__ __forceinline__ int cidx(int x, int y, int z) { return (x * 5 + y) * 5 + z; }
 
-__global__ void one_electron_kernel(int nsh, int nbf, const int* __restrict__ L, const int* __restrict__ np,
-                                    const int* __restrict__ poff, const int* __restrict__ bfo,
-                                    const double* __restrict__ ctr, const double* __restrict__ ex,
-                                    const double* __restrict__ coef, const double* __restrict__ scale, int natom,
-                                    const double* __restrict__ axyz, const double* __restrict__ Zc,
-                                    const double* __restrict__ boys_tab, double ox, double oy, double oz,
-                                    double* S, double* Tm, double* V, double* M)
+// One thread per (molecule, shell, shell) of the batched layout; each
+// molecule sees only its own nuclei.
+__global__ void one_electron_kernel(int nmol, int ld, int lds, const int* __restrict__ mol_nsh,
+                                    const int* __restrict__ mol_sho, const int* __restrict__ mol_bfo,
+                                    const int* __restrict__ mol_atom_off, const int* __restrict__ L,
+                                    const int* __restrict__ np, const int* __restrict__ poff,
+                                    const int* __restrict__ bfo, const double* __restrict__ ctr,
+                                    const double* __restrict__ ex, const double* __restrict__ coef,
+                                    const double* __restrict__ scale, const double* __restrict__ axyz,
+                                    const double* __restrict__ Zc, const double* __restrict__ boys_tab, double ox,
+                                    double oy, double oz, double* S, double* Tm, double* V, double* M)
 {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= nsh * nsh) return;
-    const int sa = p / nsh, sb = p % nsh;
+    const size_t sslot = (size_t)lds * lds;
+    const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= sslot * nmol) return;
+    const int mol = (int)(p / sslot);
+    const int la_loc = (int)((p / lds) % lds), lb_loc = (int)(p % lds);
+    if (la_loc >= mol_nsh[mol] || lb_loc >= mol_nsh[mol]) return;
+    const int sa = mol_sho[mol] + la_loc, sb = mol_sho[mol] + lb_loc;
+    const int a0 = mol_atom_off[mol], a1 = mol_atom_off[mol + 1];
+    const size_t mbase = (size_t)mol * ld * ld, mstride = (size_t)nmol * ld * ld;
+    const int f0 = mol_bfo[mol];
     const int la = L[sa], lb = L[sb];
     const int na = ncart(la), nb = ncart(lb);
     int ca[6][3], cb[6][3];
@@ -97,7 +108,7 @@ __global__ void one_electron_kernel(int nsh, int nbf, const int* __restrict__ L,
             const int lt = la + lb;
             double Vt[125];  // (e|0) for each e, m = 0 after the recursion
             for (int k = 0; k < 125; ++k) Vt[k] = 0.0;
-            for (int C = 0; C < natom; ++C) {
+            for (int C = a0; C < a1; ++C) {
                 double PC[3], PC2 = 0.0;
                 for (int x = 0; x < 3; ++x) { PC[x] = P[x] - axyz[3 * C + x]; PC2 += PC[x] * PC[x]; }
                 double F[5];
@@ -169,12 +180,12 @@ __global__ void one_electron_kernel(int nsh, int nbf, const int* __restrict__ L,
         for (int w = 0; w < nb; ++w) {
             const int r = bfo[sa] + u, c = bfo[sb] + w;
             const double f = scale[r] * scale[c];
-            const size_t o = (size_t)r * nbf + c;
+            const size_t o = mbase + (size_t)(r - f0) * ld + (c - f0);
             if (S) S[o] = f * s_acc[u * nb + w];
             if (Tm) Tm[o] = f * t_acc[u * nb + w];
             if (V) V[o] = f * v_acc[u * nb + w];
             if (M)
-                for (int x = 0; x < 3; ++x) M[(size_t)x * nbf * nbf + o] = f * m_acc[x][u * nb + w];
+                for (int x = 0; x < 3; ++x) M[(size_t)x * mstride + o] = f * m_acc[x][u * nb + w];
         }
 }
 
@@ -187,10 +198,20 @@ extern "C" int cq_one_electron(cq_basis* b, double* S, double* T, double* V, dou
 {
     if (!b) { set_error("cq_one_electron: NULL basis"); return CQ_ERR_INVALID_ARG; }
     const double o[3] = {origin ? origin[0] : 0.0, origin ? origin[1] : 0.0, origin ? origin[2] : 0.0};
-    const int nt = b->nsh * b->nsh;
-    one_electron_kernel<<<(nt + 63) / 64, 64, 0, (cudaStream_t)stream>>>(
-        b->nsh, b->nbf, b->d_L, b->d_nprim, b->d_poff, b->d_bfo, b->d_ctr, b->d_exps, b->d_coef, b->d_scale,
-        b->natom, b->d_axyz, b->d_Z, b->d_boys, o[0], o[1], o[2], S, T, V, M);
+    cudaStream_t s = (cudaStream_t)stream;
+    // padding elements of the batched layout are zero
+    const size_t ms = (size_t)b->mstride;
+    if (b->nmol > 1) {
+        if (S) CQ_CUDA(cudaMemsetAsync(S, 0, ms * sizeof(double), s));
+        if (T) CQ_CUDA(cudaMemsetAsync(T, 0, ms * sizeof(double), s));
+        if (V) CQ_CUDA(cudaMemsetAsync(V, 0, ms * sizeof(double), s));
+        if (M) CQ_CUDA(cudaMemsetAsync(M, 0, 3 * ms * sizeof(double), s));
+    }
+    const size_t nt = (size_t)b->nmol * b->lds * b->lds;
+    one_electron_kernel<<<(unsigned)((nt + 63) / 64), 64, 0, s>>>(
+        b->nmol, b->ld, b->lds, b->d_mol_nsh, b->d_mol_sho, b->d_mol_bfo, b->d_mol_atom_off, b->d_L, b->d_nprim,
+        b->d_poff, b->d_bfo, b->d_ctr, b->d_exps, b->d_coef, b->d_scale, b->d_axyz, b->d_Z, b->d_boys, o[0], o[1],
+        o[2], S, T, V, M);
     CQ_CUDA(cudaGetLastError());
     return CQ_OK;
 }
