@@ -253,6 +253,8 @@ int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
  * ld x ld slots.  nocc: host array of nmol occupied-orbital counts.  D_in
  * (device, batched layout, may be NULL for the core guess), D_out (device,
  * batched layout), E_out and iters_out (host arrays of nmol, may be NULL).
+ * A supplied D_in need not be idempotent: the first iteration diagonalises
+ * its Fock matrix without adding it to the DIIS subspace.
  * Options as for cq_scf (incremental builds are not used here).  Each
  * molecule converges on its own (its density is then frozen); returns
  * CQ_ERR_NOT_CONVERGED if any molecule reached max_iter.  stats->iterations
@@ -293,6 +295,39 @@ typedef struct {
 } cq_rt_obs;
 int cq_rt_step(cq_basis* b, const cq_rt_opts* opts, int step, void* P_prev,
                void* P_cur, cq_rt_obs* obs, void* stream);
+
+/* Learned initial density (a build requirement; no paper counterpart -- the
+ * paper's SCF starts from standard guesses).  An MLP (40 -> 256 -> 256 ->
+ * 1472, SiLU) maps an atom-pair descriptor to that pair's density block in
+ * the even-tempered s,p,d basis (H 3s1p = 6 functions, C/N/O 4s3p2d = 25);
+ * heads: 0 H on-site, 1 heavy on-site, 2 H-H, 3 H-heavy (H rows), 4
+ * heavy-heavy.  Parameters: device float array of cq_mlp_param_count().
+ *   cq_mlp_init        seeded initialisation.
+ *   cq_guess_dataset   descriptors X (npair x 40 f32), targets T (npair x
+ *                      1472 f32, the converged D blocks) and heads (npair
+ *                      i32) of every atom pair of a batched basis; D in the
+ *                      batched layout (may be NULL with T NULL).  X, T,
+ *                      head may be NULL to only count (*npair).
+ *   cq_mlp_loss_grad   masked MSE and its gradient for n samples.
+ *   cq_mlp_train       Adam over `epochs` shuffled passes (minibatch rows).
+ *   cq_guess_density   guess D (batched layout) for every molecule:
+ *                      assembled blocks (flags bit 0: on-site blocks only),
+ *                      Tr(DS) = nocc[m], npurify McWeeny steps.  Pass it as D_in to cq_scf_batch; the SCF
+ *                      decides the answer, the guess only changes the
+ *                      iteration count.
+ * Returns CQ_ERR_UNSUPPORTED if an atom does not carry that basis. */
+size_t cq_mlp_param_count(void);
+int cq_mlp_init(float* params, unsigned long long seed, void* stream);
+int cq_guess_dataset(cq_basis* b, const double* D, float* X, float* T,
+                     int* head, int* npair, void* stream);
+int cq_mlp_loss_grad(const float* params, int n, const float* X,
+                     const float* T, const int* head, float* grad,
+                     double* loss, void* stream);
+int cq_mlp_train(float* params, int n, const float* X, const float* T,
+                 const int* head, int epochs, int batch, float lr,
+                 unsigned long long seed, double* last_loss, void* stream);
+int cq_guess_density(cq_basis* b, const float* params, const int* nocc,
+                     int npurify, int flags, double* D, void* stream);
 
 /* Number of orthonormal functions (columns of X) and dropped overlap
  * eigenvectors; computes the one-electron data on first use. */

@@ -98,6 +98,13 @@ def lib():
         L.cq_basis_layout.argtypes = [vp, ip, ip, ip]
         L.cq_scf_batch.argtypes = [vp, ip, ctypes.POINTER(SCFOpts), vp, vp, dp, ip, ctypes.POINTER(SCFStats), vp]
         L.cq_nuclear_repulsion_batch.argtypes = [vp, dp]
+        L.cq_mlp_param_count.restype = ctypes.c_size_t
+        L.cq_mlp_init.argtypes = [vp, ctypes.c_ulonglong, vp]
+        L.cq_guess_dataset.argtypes = [vp, vp, vp, vp, vp, ip, vp]
+        L.cq_mlp_loss_grad.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, dp, vp]
+        L.cq_mlp_train.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                   ctypes.c_ulonglong, dp, vp]
+        L.cq_guess_density.argtypes = [vp, vp, ip, ctypes.c_int, ctypes.c_int, vp, vp]
         L.cq_fock_set_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_get_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
@@ -405,3 +412,52 @@ class Basis:
             with open(path, "w") as fh:
                 json.dump(data, fh, indent=1)
         return out
+
+
+class DensityGuessMLP:
+    """Learned initial density (see cq_mlp_* / cq_guess_* in include/cq.h)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        import torch
+        self.n = int(lib().cq_mlp_param_count())
+        self.params = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        check(lib().cq_mlp_init(_ptr(self.params), seed, _stream_ptr(stream)), "cq_mlp_init")
+
+    @staticmethod
+    def dataset(basis, D=None, stream=None):
+        """(X, T, head) of every atom pair of a batched basis; T from D."""
+        import torch
+        npair = ctypes.c_int()
+        check(lib().cq_guess_dataset(basis.h, None, None, None, None, ctypes.byref(npair),
+                                     _stream_ptr(stream)), "cq_guess_dataset")
+        n = npair.value
+        X = torch.empty((n, 40), dtype=torch.float32, device="cuda")
+        H = torch.empty(n, dtype=torch.int32, device="cuda")
+        T = torch.empty((n, 1472), dtype=torch.float32, device="cuda") if D is not None else None
+        check(lib().cq_guess_dataset(basis.h, _ptr(D) if D is not None else None, _ptr(X),
+                                     _ptr(T) if T is not None else None, _ptr(H), ctypes.byref(npair),
+                                     _stream_ptr(stream)), "cq_guess_dataset")
+        return X, T, H
+
+    def loss_grad(self, X, T, H, stream=None):
+        import torch
+        g = torch.empty_like(self.params)
+        loss = ctypes.c_double()
+        check(lib().cq_mlp_loss_grad(_ptr(self.params), int(X.shape[0]), _ptr(X), _ptr(T), _ptr(H),
+                                     _ptr(g), ctypes.byref(loss), _stream_ptr(stream)), "cq_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, X, T, H, epochs=20, batch=2048, lr=1e-3, seed=0, stream=None):
+        loss = ctypes.c_double()
+        check(lib().cq_mlp_train(_ptr(self.params), int(X.shape[0]), _ptr(X), _ptr(T), _ptr(H), epochs,
+                                 batch, lr, seed, ctypes.byref(loss), _stream_ptr(stream)), "cq_mlp_train")
+        return loss.value
+
+    def guess(self, basis, nocc, npurify=0, onsite_only=False, stream=None):
+        import torch
+        D = torch.empty((basis.nmol, basis.ld, basis.ld), dtype=torch.float64, device="cuda")
+        no = np.ascontiguousarray(nocc, dtype=np.int32)
+        check(lib().cq_guess_density(basis.h, _ptr(self.params), no.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                     npurify, int(bool(onsite_only)), _ptr(D), _stream_ptr(stream)),
+              "cq_guess_density")
+        return D

@@ -20,7 +20,7 @@ NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                   "--expt-relaxed-constexpr", "-Xptxas=-warn-spills", "-I", CSRC, "-I", GEN,
                   "-I", os.path.join(os.path.dirname(HERE), "include")]
 HAND_SOURCES = ["cq_basis.cu", "cq_fock.cu", "cq_peaks.cu", "cq_noalloc.cu", "cq_oneint.cu", "cq_drivers.cu",
-                "cq_coop.cu", "cq_batch.cu"]
+                "cq_coop.cu", "cq_batch.cu", "cq_mlp.cu"]
 LIBS = ["-lcublas", "-lcusolver"]
 
 PCS = [(0, 0), (1, 0), (1, 1), (2, 0), (2, 1), (2, 2)]

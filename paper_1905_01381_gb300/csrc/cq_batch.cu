@@ -422,6 +422,13 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
         open = (int)hopen;
         if (open == 0) break;
         if (cudaMemcpyAsync(Eold, E, nmol * sizeof(double), cudaMemcpyDeviceToDevice, s)) return fail(CQ_ERR_CUDA);
+        // a supplied starting density need not be idempotent: its Fock matrix
+        // is diagonalised as it is and kept out of the DIIS subspace
+        if (it == 1 && D_in) {
+            if ((rc = density_from(F, Dn))) return fail(rc);
+            freeze_update_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, conv, Dn, D);
+            continue;
+        }
         // DIIS
         const int slot = head;
         head = (head + 1) % o.diis_size;
