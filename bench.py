@@ -351,6 +351,186 @@ def run_gpu(args):
     return 0
 
 
+def _driver_setup():
+    import torch
+    import paper_1905_01381_gb300 as cq
+    ws, rk, lr = dist_env()
+    if ws > 1:
+        # the driver workloads are single-GPU runs: replicas print nothing
+        if rk != 0:
+            return None, None
+    torch.cuda.set_device(lr)
+    cq.build()
+    return torch, cq
+
+
+def _line(metric, value, unit, hib, args, ms, config, extra, clk, launches):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": config,
+           "gpu_launches": launches, "clocks": clk.summary()}
+    out.update(extra)
+    print(json.dumps(out))
+
+
+def run_scf(args):
+    """RHF direct SCF on the 16-atom workload: time to the converged energy,
+    all-FP64 against mixed precision with incremental builds."""
+    torch, cq = _driver_setup()
+    if cq is None:
+        return 0
+    mol, bas = synth.workload_rt16()
+    b = cq.Basis(mol, bas)
+    nocc = mol.n_electrons() // 2
+    P = torch.as_tensor(synth.density(b.nbf, nocc, 5), device="cuda")
+    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    for _ in range(args.warmup):
+        b.fock_build(P)
+    modes = {"fp64": dict(prec=cq.CQ_PREC_FP64),
+             "mixed": dict(prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, incremental=True, switch_tol=1e-5)}
+    res = {}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, kw in modes.items():
+            ts, st = [], None
+            for _ in range(args.steps):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                _, _, st = b.scf(nocc, **kw)
+                torch.cuda.synchronize()
+                ts.append(time.perf_counter() - t0)
+            res[name] = {"s": statistics.median(ts), "energy": st["energy"], "iterations": st["iterations"],
+                         "quartets_fp64": st["quartets_fp64"], "quartets_fp32": st["quartets_fp32"]}
+    dE = abs(res["mixed"]["energy"] - res["fp64"]["energy"])
+    b.close()
+    _line("RHF SCF time to converged energy (mixed + incremental vs FP64)", res["mixed"]["s"], "s", False, args,
+          res["mixed"]["s"] * 1e3,
+          {"workload": WORKLOAD.replace("complex-Hermitian P (29 occ)", "RHF, 29 doubly occupied"),
+           "e_tol": 1e-10, "d_tol": 1e-8, "mixed_tol": MIXED_TOL, "switch_tol": 1e-5},
+          {"fp64_s": res["fp64"]["s"], "speedup_vs_fp64": res["fp64"]["s"] / res["mixed"]["s"],
+           "dE_mixed_vs_fp64_Eh": dE, "runs": res}, clk, None)
+    return 0
+
+
+def run_rt(args):
+    """RT-TDHF (MMUT with EM2 restarts) from the RHF ground state of the
+    16-atom workload, delta kick 1e-4 au along z for the first step:
+    steps/s in FP64 and mixed precision, and the observables' agreement."""
+    torch, cq = _driver_setup()
+    if cq is None:
+        return 0
+    mol, bas = synth.workload_rt16()
+    b = cq.Basis(mol, bas)
+    nocc = mol.n_electrons() // 2
+    D, _, st = b.scf(nocc, d_tol=1e-10)
+    P0 = D.to(torch.complex128)
+    b.autotune(P0, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    dt = 0.05
+    field = dict(field=(0.0, 0.0, 1e-4), t_on=0.0, t_off=dt)
+    traces, rates = {}, {}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, kw in (("fp64", dict(prec=cq.CQ_PREC_FP64)),
+                         ("mixed", dict(prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL))):
+            Pp, Pc = P0.clone(), P0.clone()
+            for k in range(args.warmup):
+                b.rt_step(k, Pp, Pc, dt=dt, **field, **kw)
+            Pp, Pc = P0.clone(), P0.clone()
+            obs = []
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for k in range(args.rt_steps):
+                obs.append(b.rt_step(k, Pp if k else None, Pc, dt=dt, **field, **kw))
+            torch.cuda.synchronize()
+            rates[name] = args.rt_steps / (time.perf_counter() - t0)
+            traces[name] = obs
+    mu = {k: np.array([o["dipole"][2] for o in v]) for k, v in traces.items()}
+    tr = {k: np.array([o["trPS"] for o in v]) for k, v in traces.items()}
+    en = {k: np.array([o["energy"] for o in v]) for k, v in traces.items()}
+    b.close()
+    _line("RT-TDHF MMUT/EM2 steps/s (mixed vs FP64)", rates["mixed"], "steps/s", True, args,
+          1e3 / rates["mixed"],
+          {"workload": WORKLOAD.replace("complex-Hermitian P (29 occ)", "RHF ground state, delta kick 1e-4 au z"),
+           "dt": dt, "steps": args.rt_steps, "restart_every": 50, "mixed_tol": MIXED_TOL},
+          {"fp64_steps_per_s": rates["fp64"],
+           "max_abs_dmu_z_mixed_vs_fp64": float(np.abs(mu["mixed"] - mu["fp64"]).max()),
+           "mu_z_response_range": float(np.ptp(mu["fp64"])),
+           "max_abs_trPS_minus_nocc": {k: float(np.abs(v - nocc).max()) for k, v in tr.items()},
+           "energy_drift_after_kick_Eh": {k: float(np.ptp(v[2:])) for k, v in en.items()},
+           "ground_state_energy": st["energy"]}, clk, None)
+    return 0
+
+
+def run_batch(args):
+    """Batched RHF over many uneven molecules (4-12 atoms, single-primitive
+    even-tempered s,p,d shells) with the iterations replayed from a captured
+    graph; the learned guess trained on batched SCF solutions of other
+    molecules, against the core-Hamiltonian guess at identical energies."""
+    torch, cq = _driver_setup()
+    if cq is None:
+        return 0
+    t_all = time.perf_counter()
+    train = synth.workload_batch(args.ntrain, rep=1, max_depth=1)
+    test = synth.workload_batch(args.nmol, rep=0, max_depth=1)
+    no = lambda items: [m.n_electrons(m.closed_shell_charge()) // 2 for m, _ in items]
+    btr, bte = cq.Basis.batch(train), cq.Basis.batch(test)
+    Pw = torch.zeros((bte.nmol, bte.ld, bte.ld), dtype=torch.float64, device="cuda")
+    for m, n in enumerate(bte.mol_n):
+        Pw[m, :n, :n] = torch.as_tensor(synth.density(n, no(test)[m], m))
+    bte.autotune(Pw, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    for qc in range(21):
+        for p in (0, 1):
+            btr.set_variant(qc, p, bte.get_variant(qc, p))
+    # training data: converged FP64 solutions of the training molecules
+    t0 = time.perf_counter()
+    Dtr, _, ittr, sttr = btr.scf_batch(no(train), raise_on_fail=False)
+    t_train_scf = time.perf_counter() - t0
+    ok = [i for i in range(btr.nmol) if ittr[i] < 128]
+    keep = [train[i] for i in ok]
+    bk = cq.Basis.batch(keep)
+    Dk = bk.pack([btr.unpack(Dtr)[i] for i in ok])
+    net = cq.DensityGuessMLP(seed=7)
+    X, T, H = net.dataset(bk, Dk)
+    loss0, _ = net.loss_grad(X, T, H)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = net.train(X, T, H, epochs=150, batch=256, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    t_fit = time.perf_counter() - t0
+    nocc = no(test)
+    runs = {}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, prec, learned in (("core_fp64", cq.CQ_PREC_FP64, False), ("learned_fp64", cq.CQ_PREC_FP64, True),
+                                    ("core_mixed", cq.CQ_PREC_MIXED, False),
+                                    ("learned_mixed", cq.CQ_PREC_MIXED, True)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            D0 = net.guess(bte, nocc) if learned else None
+            _, E, it, st = bte.scf_batch(nocc, prec=prec, mixed_tol=MIXED_TOL, D0=D0, raise_on_fail=False)
+            torch.cuda.synchronize()
+            runs[name] = {"s": time.perf_counter() - t0, "E": E, "it": it, "st": st}
+    base = runs["core_fp64"]
+    conv = base["it"] < 128
+    summary = {}
+    for name, r in runs.items():
+        same = conv & (r["it"] < 128) & (np.abs(r["E"] - base["E"]) <= 1e-8)
+        summary[name] = {"s": round(r["s"], 3), "batched_iterations": r["st"]["iterations"],
+                         "converged": int((r["it"] < 128).sum()), "same_energy_as_core_fp64": int(same.sum()),
+                         "mean_iterations_same": float(r["it"][same].mean()) if same.any() else None,
+                         "quartets_fp64": r["st"]["quartets_fp64"], "quartets_fp32": r["st"]["quartets_fp32"],
+                         "graph": r["st"]["graph"]}
+    best = runs["learned_mixed"]
+    _line("batched RHF time to converged energies, learned guess + mixed vs core guess FP64",
+          bte.nmol / best["s"], "molecules/s", True, args, best["s"] * 1e3,
+          {"workload": f"{bte.nmol} molecules of 4-12 atoms (H/C/N/O), single-primitive even-tempered "
+                       f"s,p,d shells, {min(bte.mol_n)}-{max(bte.mol_n)} functions",
+           "training_molecules": len(ok), "training_pairs": int(X.shape[0]), "e_tol": 1e-10, "d_tol": 1e-8,
+           "mixed_tol": MIXED_TOL},
+          {"core_fp64_molecules_per_s": bte.nmol / base["s"],
+           "speedup_vs_core_fp64": base["s"] / best["s"], "runs": summary,
+           "training": {"scf_s": t_train_scf, "fit_s": t_fit, "loss0": loss0, "loss": loss},
+           "wall_s": time.perf_counter() - t_all}, clk, None)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -361,9 +541,21 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-stride", type=int, default=150)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch"],
+                    help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
+                         "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")
+    ap.add_argument("--rt-steps", type=int, default=100)
+    ap.add_argument("--nmol", type=int, default=512)
+    ap.add_argument("--ntrain", type=int, default=512)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "scf":
+        return run_scf(args)
+    if args.workload == "rt":
+        return run_rt(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_gpu(args)
 
 

@@ -236,6 +236,7 @@ typedef struct {
     int incremental;     /* 0/1 */
     int full_every;      /* 8 */
     double switch_tol;   /* 1e-5 */
+    int graph;           /* cq_scf_batch: 1 = capture the iteration as a CUDA graph */
 } cq_scf_opts;
 typedef struct {
     double energy;
@@ -243,6 +244,8 @@ typedef struct {
     double last_rms;
     unsigned long long quartets_fp64, quartets_fp32;  /* summed over iterations */
     double ms;
+    int graph;           /* cq_scf_batch: 2 whole iteration replayed as a graph,
+                            1 graphs around an eager eigensolver call, 0 eager */
 } cq_scf_stats;
 int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
            double* D_out, double* F_out, cq_scf_stats* stats, void* stream);
@@ -256,10 +259,19 @@ int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
  * A supplied D_in need not be idempotent: the first iteration diagonalises
  * its Fock matrix without adding it to the DIIS subspace.
  * Options as for cq_scf (incremental builds are not used here).  Each
- * molecule converges on its own (its density is then frozen); returns
- * CQ_ERR_NOT_CONVERGED if any molecule reached max_iter.  stats->iterations
- * is the number of batched iterations, stats->converged the number of
- * converged molecules, stats->energy the sum of the energies. */
+ * molecule converges on its own: its density is then frozen and later
+ * builds skip its quartets.  With prec = CQ_PREC_MIXED a molecule's builds
+ * move to all-FP64 once its orthogonal-basis commutator rms falls below
+ * switch_tol, and convergence is only declared on an all-FP64 energy.
+ * The state of an iteration (iteration number, DIIS ring, convergence
+ * flags) lives on the device, so with opts->graph the iterations after the
+ * first are captured once as a CUDA graph and replayed; the host reads the
+ * number of open molecules one iteration behind (at most one extra, no-op
+ * iteration).  Runs on a private stream ordered after `stream`; returns
+ * after it has drained.  Returns CQ_ERR_NOT_CONVERGED if any molecule
+ * reached max_iter.  stats->iterations is the number of batched iterations,
+ * stats->converged the number of converged molecules, stats->energy the sum
+ * of the energies, stats->graph how the iterations were launched. */
 int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opts,
                  const double* D_in, double* D_out, double* E_out,
                  int* iters_out, cq_scf_stats* stats, void* stream);

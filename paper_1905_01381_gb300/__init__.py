@@ -40,13 +40,13 @@ class SCFOpts(ctypes.Structure):
     _fields_ = [("e_tol", ctypes.c_double), ("d_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("prec", ctypes.c_int), ("mixed_tol", ctypes.c_double),
                 ("schwarz_tol", ctypes.c_double), ("incremental", ctypes.c_int), ("full_every", ctypes.c_int),
-                ("switch_tol", ctypes.c_double)]
+                ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int)]
 
 
 class SCFStats(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("last_rms", ctypes.c_double), ("quartets_fp64", ctypes.c_ulonglong),
-                ("quartets_fp32", ctypes.c_ulonglong), ("ms", ctypes.c_double)]
+                ("quartets_fp32", ctypes.c_ulonglong), ("ms", ctypes.c_double), ("graph", ctypes.c_int)]
 
 
 class RTOpts(ctypes.Structure):
@@ -219,14 +219,14 @@ class Basis:
 
     def scf_batch(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
                   mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, D0=None, stream=None,
-                  raise_on_fail=True):
+                  raise_on_fail=True, graph=True):
         """Batched RHF; returns (D batched tensor, energies, iterations, stats)."""
         import torch
         D = torch.empty((self.nmol, self.ld, self.ld), dtype=torch.float64, device="cuda")
         no = np.ascontiguousarray(nocc, dtype=np.int32)
         E = np.zeros(self.nmol)
         it = np.zeros(self.nmol, dtype=np.int32)
-        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol)
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, int(bool(graph)))
         st = SCFStats()
         ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
         rc = lib().cq_scf_batch(self.h, no.ctypes.data_as(ip), ctypes.byref(o),
@@ -235,7 +235,8 @@ class Basis:
         if raise_on_fail:
             check(rc, "cq_scf_batch")
         return D, E, it, {"iterations": st.iterations, "converged": st.converged, "ms": st.ms,
-                          "quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32, "rc": rc}
+                          "quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32, "rc": rc,
+                          "graph": st.graph}
 
     def close(self):
         if getattr(self, "h", None):
@@ -258,6 +259,13 @@ class Basis:
         E = ctypes.c_double()
         check(lib().cq_nuclear_repulsion(self.h, ctypes.byref(E)), "cq_nuclear_repulsion")
         return E.value
+
+    def nuclear_repulsion_batch(self):
+        """Nuclear repulsion of every molecule of a batched basis."""
+        E = np.zeros(self.nmol)
+        check(lib().cq_nuclear_repulsion_batch(self.h, E.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+              "cq_nuclear_repulsion_batch")
+        return E
 
     def fock_build(self, P, kind=None, schwarz_tol=1e-14, mixed_tol=1e-5, prec=CQ_PREC_FP64,
                    want_J=True, want_K=True, J=None, K=None, stats=False, stream=None):

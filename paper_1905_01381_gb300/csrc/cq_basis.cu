@@ -169,6 +169,8 @@ static void free_basis(cq_basis* b)
         if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
     }
     if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    if (b->batch_stream) cudaStreamDestroy(b->batch_stream);
+    if (b->batch_ev) cudaEventDestroy(b->batch_ev);
     delete b;
 }
 

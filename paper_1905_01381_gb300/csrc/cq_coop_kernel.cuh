@@ -67,9 +67,13 @@ __global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, i
         m = fmaxf(m, fmaxf(__ldg(Ds + B.sa * ns + K.sa), __ldg(Ds + B.sa * ns + K.sb)));
         m = fmaxf(m, fmaxf(__ldg(Ds + B.sb * ns + K.sa), __ldg(Ds + B.sb * ns + K.sb)));
         const float bound = __ldg(a.Q + ib) * __ldg(a.Q + j) * m;
-        bool sel = bound >= a.tau;
-        if (a.prec_sel == 1) sel = sel && bound >= a.tau_mixed;
-        else if (a.prec_sel == 2) sel = sel && bound < a.tau_mixed;
+        // a molecule in all-FP64 mode sends every survivor to the FP64 half;
+        // a skipped molecule has none
+        const int mode = a.mol_mode ? __ldg(a.mol_mode + B.smbase / a.lds2) : 1;
+        const float tm = (mode & 1) ? a.tau_mixed : 0.f;
+        bool sel = bound >= a.tau && !(mode & 2);
+        if (a.prec_sel == 1) sel = sel && bound >= tm;
+        else if (a.prec_sel == 2) sel = sel && bound < tm;
         if (!sel) return;
     }
     const int NA = ncart(C.la), NB = ncart(C.lb), NC = ncart(C.lc), ND = ncart(C.ld);

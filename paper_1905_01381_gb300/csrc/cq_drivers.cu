@@ -351,7 +351,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
                       double* F_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !D_out) { set_error("cq_scf: NULL basis or output"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0};
     if (opts) o = *opts;
     const int n = b->nbf;
     if (b->nmol > 1) { set_error("cq_scf: batched basis; use cq_scf_batch"); return CQ_ERR_UNSUPPORTED; }

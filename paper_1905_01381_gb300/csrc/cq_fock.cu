@@ -54,14 +54,14 @@ __global__ void density_prep_kernel(int kind, int nmol, int ld, const int* __res
 // per molecule (lds = the largest molecule's shell count).
 __global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ mol_nsh, const int* __restrict__ mol_sho,
                             const int* __restrict__ mol_bfo, const int* __restrict__ bfo, int nk,
-                            const double* __restrict__ Dp, float* __restrict__ Dmax)
+                            const double* __restrict__ Dp, const int* __restrict__ mol_mode, float* __restrict__ Dmax)
 {
     const size_t sslot = (size_t)lds * lds;
     const size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= sslot * nmol) return;
     const int m = (int)(p / sslot);
     const int sa = (int)((p / lds) % lds), sb = (int)(p % lds);
-    if (sa >= mol_nsh[m] || sb >= mol_nsh[m]) { Dmax[p] = 0.f; return; }
+    if (sa >= mol_nsh[m] || sb >= mol_nsh[m] || (mol_mode && (mol_mode[m] & 2))) { Dmax[p] = 0.f; return; }
     const int a = mol_sho[m] + sa, b = mol_sho[m] + sb, f0 = mol_bfo[m];
     const size_t slot = (size_t)ld * ld, ms = slot * nmol;
     double mx = 0.0;
@@ -134,9 +134,9 @@ int ensure_scratch(cq_basis* b, int nk)
 // returns this lane's class of candidate j0 + lane (-1 rejected, 0 FP64,
 // 1 FP32).
 __device__ __forceinline__ int classify_one(const ClassifyArgs& c, const float* Dm, int j, int jend, int ba, int bb,
-                                            float Qb, float dab)
+                                            float Qb, float dab, int mode)
 {
-    if (j >= jend) return -1;
+    if (j >= jend || (mode & 2)) return -1;
     const int ns = c.nsh;
     const int kc = __ldg(&c.pairs[j].sa), kd = __ldg(&c.pairs[j].sb);
     float m = fmaxf(dab, __ldg(Dm + kc * ns + kd));
@@ -144,7 +144,7 @@ __device__ __forceinline__ int classify_one(const ClassifyArgs& c, const float* 
     m = fmaxf(m, fmaxf(__ldg(Dm + bb * ns + kc), __ldg(Dm + bb * ns + kd)));
     const float bound = Qb * __ldg(c.Q + j) * m;
     if (!(bound >= c.tau)) return -1;
-    return (c.split && bound < c.tau_mixed) ? 1 : 0;
+    return ((mode & 1) && bound < c.tau_mixed) ? 1 : 0;
 }
 
 // Pass 1 (write = 0): survivors per task and precision -> tcount[2t + p].
@@ -165,14 +165,16 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
     const int ib = t.x;
     const int ba = __ldg(&c.pairs[ib].sa), bb = __ldg(&c.pairs[ib].sb);
     const float Qb = __ldg(c.Q + ib);
-    const float* Dm = c.Dmax + __ldg(&c.pairs[ib].smbase);
+    const long long smb = __ldg(&c.pairs[ib].smbase);
+    const float* Dm = c.Dmax + smb;
     const float dab = __ldg(Dm + ba * c.nsh + bb);
+    const int mode = c.mol_mode ? (__ldg(c.mol_mode + smb / c.lds2) & (c.split ? 3 : 2)) : (c.split ? 1 : 0);
     const long long base = c.cls_qoff[qc], top = c.cls_qoff[qc + 1];
     unsigned int n0 = 0, n1 = 0;
     unsigned int o0 = write ? toff[2 * w] : 0, o1 = write ? toff[2 * w + 1] : 0;
     for (int j0 = t.y; j0 < t.z; j0 += 32) {
         const int j = j0 + lane;
-        const int prec = classify_one(c, Dm, j, t.z, ba, bb, Qb, dab);
+        const int prec = classify_one(c, Dm, j, t.z, ba, bb, Qb, dab, mode);
         const unsigned m0 = __ballot_sync(0xffffffffu, prec == 0);
         const unsigned m1 = __ballot_sync(0xffffffffu, prec == 1);
         if (write) {
@@ -225,9 +227,12 @@ __global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const un
 
 // Screen and split every candidate quartet into the per-class lists (one
 // kernel), then launch every class kernel, heaviest classes first.
-int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s)
+int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s,
+                        const int* mol_mode)
 {
     ClassifyArgs c;
+    c.mol_mode = mol_mode;
+    c.lds2 = (long long)b->lds * b->lds;
     c.pairs = b->d_pairs; c.tasks = b->d_tasks; c.ntasks = b->task_off[NQC];
     c.cls_task_off = b->d_task_off; c.cls_qoff = b->d_qoff;
     c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->lds;
@@ -331,8 +336,17 @@ extern "C" int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* var
     return CQ_OK;
 }
 
-extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
-                             const cq_fock_opts* opts, cq_fock_stats* stats, void* stream)
+// Adds the four totals (FP64 quartets, FP64 primitive quartets, FP32
+// quartets, FP32 primitive quartets) of a build into a running accumulator.
+namespace cq {
+__global__ void counter_accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ acc)
+{
+    if (threadIdx.x < 4) acc[threadIdx.x] += c[threadIdx.x];
+}
+}  // namespace cq
+
+int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* K, const cq_fock_opts* opts,
+                     cq_fock_stats* stats, cudaStream_t s, const int* mol_mode, unsigned long long* acc)
 {
     if (!b || !P) { set_error("cq_fock_build: NULL basis or density"); return CQ_ERR_INVALID_ARG; }
     if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_PAULI4) {
@@ -357,7 +371,6 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     int rc = ensure_scratch(b, nk);
     if (rc) return rc;
     if ((rc = ensure_coop_tasks(b))) return rc;
-    cudaStream_t s = (cudaStream_t)stream;
     const int n = b->ld;
     const size_t nn = b->mstride;
     const int nb = (int)((nn + 255) / 256);
@@ -366,7 +379,8 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
                                            b->d_Dp);
     const size_t nsl = (size_t)b->nmol * b->lds * b->lds;
     dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
-                                                              b->d_mol_bfo, b->d_bfo, nk, b->d_Dp, b->d_Dmax);
+                                                              b->d_mol_bfo, b->d_bfo, nk, b->d_Dp, mol_mode,
+                                                              b->d_Dmax);
     CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
@@ -383,10 +397,13 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
     a.J = b->d_Jp; a.K = b->d_Kp;
     a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
     a.counters = b->d_cnt + 4;
-    rc = classify_and_launch(b, a, o, b->profile != 0, s);
+    a.mol_mode = mol_mode;
+    a.lds2 = (long long)b->lds * b->lds;
+    rc = classify_and_launch(b, a, o, b->profile != 0, s, mol_mode);
     if (rc) return rc;
     CQ_CUDA(cudaGetLastError());
     counter_total_kernel<<<1, 32, 0, s>>>(b->d_cnt);
+    if (acc) counter_accumulate_kernel<<<1, 32, 0, s>>>(b->d_cnt, acc);
     finalize_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, b->d_scale, b->d_Jp, b->d_Kp, J,
                                        (double*)K, o.want_J, o.want_K);
     CQ_CUDA(cudaGetLastError());
@@ -404,6 +421,12 @@ extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, vo
         stats->ms = ms;
     }
     return CQ_OK;
+}
+
+extern "C" int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
+                             const cq_fock_opts* opts, cq_fock_stats* stats, void* stream)
+{
+    return fock_build_modes(b, kind, P, J, K, opts, stats, (cudaStream_t)stream, nullptr, nullptr);
 }
 
 extern "C" int cq_fock_profile(cq_basis* b, int enable)

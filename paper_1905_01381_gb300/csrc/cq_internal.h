@@ -147,13 +147,22 @@ struct cq_basis {
     cudaEvent_t join_ev[NSIDE] = {};
     int4* d_coop_tasks = nullptr;
     bool coop_dirty = true;
+    // private stream of the batched SCF (graph capture needs a non-default stream)
+    cudaStream_t batch_stream = nullptr;
+    cudaEvent_t batch_ev = nullptr;
 };
 
 namespace cq {
 constexpr int COOP_CHUNK = 64;   // primitive quartets per cooperative task
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s);
 int ensure_coop_tasks(cq_basis* b);
-int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s);
+int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s,
+                        const int* mol_mode = nullptr);
+// cq_fock_build with an optional device array of per-molecule modes (see
+// ClassifyArgs::mol_mode) and an optional device accumulator of the four
+// quartet/primitive totals; no host synchronisation unless stats is given
+int fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* K, const cq_fock_opts* opts,
+                     cq_fock_stats* stats, cudaStream_t s, const int* mol_mode, unsigned long long* acc);
 }
 
 namespace cq {

@@ -37,6 +37,8 @@ struct JKArgs {
     const unsigned int* qcount;   // number of entries (device)
     int qdir;                     // +1: entries qlist[i]; -1: entries qlist[-i] (list filled from the back)
     long long qmax;               // capacity of the list (candidate quartets of the class)
+    const int* mol_mode;          // optional per-molecule mode (see ClassifyArgs), read by the
+    long long lds2;               // cooperative kernel, which screens its own tasks
 };
 
 template <typename R>
@@ -314,6 +316,11 @@ struct ClassifyArgs {
     int nsh;
     float tau, tau_mixed;
     int split;                    // 0: every survivor to the FP64 list
+    // optional per-molecule mode (batched drivers): bit 0 allows the FP32
+    // list for the molecule's quartets, bit 1 skips the molecule; NULL: every
+    // molecule follows `split`
+    const int* mol_mode;
+    long long lds2;               // shell-block slot size (smbase / lds2 = molecule)
     int2* qlist;
     unsigned int* qcount;         // [NQC][2]
 };

@@ -4,7 +4,7 @@
 // densities.  Hand-written kernels: FP32 tiled GEMM (forward and backward),
 // bias + SiLU, masked MSE, Adam; descriptors, block gather and scatter.
 // The guess is assembled per molecule, symmetrised, scaled to Tr(PS) = nocc
-// and McWeeny-purified (P <- 3PSP - 2PSPSP); the SCF then judges it, so only
+// and optionally McWeeny-purified (P <- 3PSP - 2PSPSP); the SCF then judges it, so only
 // the iteration count can change, never the converged answer.
 #include <cublas_v2.h>
 

@@ -23,7 +23,8 @@ __global__ void density_prep_kernel(int kind, int nmol, int ld, const int* __res
                                     const double* __restrict__ sc, double* __restrict__ Dp);
 __global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ mol_nsh, const int* __restrict__ mol_sho,
                             const int* __restrict__ mol_bfo, const int* __restrict__ bfo, int nk,
-                            const double* __restrict__ Dp, float* __restrict__ Dmax);
+                            const double* __restrict__ Dp, const int* __restrict__ mol_mode,
+                            float* __restrict__ Dmax);
 __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
                                 const int* __restrict__ mol_bfo, const double* __restrict__ sc,
                                 const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
@@ -125,7 +126,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     density_prep_kernel<<<nb, 256, 0, s>>>(kind, b->nmol, n, b->d_mol_n, b->d_mol_bfo, (const double*)P, b->d_scale, Dp);
     const size_t nsl = (size_t)b->nmol * b->lds * b->lds;
     dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
-                                                              b->d_mol_bfo, b->d_bfo, nk, Dp, Dmax);
+                                                              b->d_mol_bfo, b->d_bfo, nk, Dp, nullptr, Dmax);
     // the array keeps the previous call's contents: clear the accumulators
     CQ_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), s));
     CQ_CUDA(cudaMemsetAsync(Kp, 0, nn * nk * sizeof(double), s));

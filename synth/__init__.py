@@ -224,14 +224,14 @@ def workload_ghf40(rep: int = 0):
     return mol, basis_spd(mol, seed + 7)
 
 
-def workload_batch(nmol: int = 512, rep: int = 0):
+def workload_batch(nmol: int = 512, rep: int = 0, max_depth: int = 6):
     out = []
     g = rng(1000 * 5 + rep)
     for i in range(nmol):
         na = int(g.integers(4, 13))
         s = int(g.integers(0, 2 ** 31))
         mol = cluster(na, s, p_h=0.5)
-        out.append((mol, basis_spd(mol, s + 7)))
+        out.append((mol, basis_spd(mol, s + 7, max_depth=max_depth)))
     return out
 
 

@@ -44,9 +44,16 @@ def test_one_electron(cq):
     assert abs(b.nuclear_repulsion() - oracle.nuclear_repulsion(mol)) < 1e-12
 
 
-@pytest.mark.parametrize("case", ["triatomic", "mixed"])
+def _paper_water():
+    from golden import water_sample_input
+    mol = synth.Molecule(*water_sample_input())
+    return mol, synth.basis_triatomic(mol)
+
+
+@pytest.mark.parametrize("case", ["triatomic", "mixed", "paper_water"])
 def test_rhf_energy_matches_oracle(cq, dr, case):
-    mol, bas = synth.workload_triatomic() if case == "triatomic" else _mixed_case()
+    mol, bas = {"triatomic": synth.workload_triatomic, "mixed": _mixed_case,
+                "paper_water": _paper_water}[case]()
     nocc = mol.n_electrons(mol.closed_shell_charge()) // 2
     b = cq.Basis(mol, bas)
     D, F, st = b.scf(nocc)
