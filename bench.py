@@ -176,6 +176,33 @@ def cpu_baseline(seconds: float):
 
 
 # ---------------------------------------------------------------- GPU arm
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic_jk_rt16.json")
+KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh")
+
+
+def kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1905_01381_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_of(key, cls, variant):
+    """DRAM bytes (read + write) of one launch of a class kernel, from the
+    ncu capture summarised in profiles/ (bytes per quartet x the launch's
+    quartets); None when no capture of this kernel and variant exists or the
+    kernel sources changed since it was taken."""
+    try:
+        tj = json.load(open(TRAFFIC))
+    except (OSError, ValueError):
+        return None
+    e = tj.get("launches", {}).get(key)
+    if not e or e.get("variant") != variant or tj.get("sources_sha1") != kernel_sources_sha1():
+        return None
+    return e["bytes_per_quartet"] * cls["quartets"]
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -201,7 +228,10 @@ def run_gpu(args):
     flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # ---- kernel variant per class (autotuner; set-up, not timed)
-    tuned = b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=False)
+    if args.no_autotune:
+        tuned = {"variant": [[b.get_variant(q, 0), b.get_variant(q, 1)] for q in range(21)]}
+    else:
+        tuned = b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=False)
 
     # ---- accuracy of the timed mode against the all-FP64 build (same run)
     J64, K64 = b.fock_build(P)
@@ -263,17 +293,7 @@ def run_gpu(args):
     dv = cls[dom]
     dom_peak = peak32 if dv["fp32"] else peak64
     achieved = dv["flops"] / (dv["ms"] * 1e-3)
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            src = open(os.path.join(ROOT, "paper_1905_01381_gb300", "csrc", "cq_jk.cuh")).read()
-            import hashlib
-            if tj.get("kernel") == dom and tj.get("cq_jk_sha1") == hashlib.sha1(src.encode()).hexdigest():
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = traffic_of(dom, dv, b.get_variant(dv["qc"], dv["fp32"]))
 
     # ---- FP64-only rate (reported beside the headline)
     fp64_rate = None
@@ -541,6 +561,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-stride", type=int, default=150)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel variant per class (profiling runs)")
     ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
                          "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")

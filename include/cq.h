@@ -237,6 +237,9 @@ typedef struct {
     int full_every;      /* 8 */
     double switch_tol;   /* 1e-5 */
     int graph;           /* cq_scf_batch: 1 = capture the iteration as a CUDA graph */
+    int guess_fallback;  /* cq_scf_batch with D_in: a molecule still open at this
+                            iteration (> 1) restarts from the core guess with a
+                            fresh DIIS subspace; 0 = never */
 } cq_scf_opts;
 typedef struct {
     double energy;
@@ -249,6 +252,23 @@ typedef struct {
 } cq_scf_stats;
 int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
            double* D_out, double* F_out, cq_scf_stats* stats, void* stream);
+
+/* Two-component (GHF) SCF in the Pauli representation (Eq. pauli_sep,
+ * Eq. 2c_fock with the factor-2 reading of J): per iteration one Fock build
+ * of kind CQ_DENS_PAULI4, F^0 = h + 2J[P^0] - K[P^0], F^k = -K[P^k]; the
+ * 2n x 2n Fock matrix sum_I sigma_I (x) F^I is diagonalised in the
+ * orthonormal basis diag(X, X) and the nelec lowest spinors give
+ * P^{2C} = C C^+, whose Pauli components are the next density.
+ * E = sum_I Re Tr[(h^I + F^I) P^I] + E_nuc (h^k = 0).  DIIS on
+ * X^+(F P S - S P F)X with real B_ij = Re <e_i|e_j>.  Options as for cq_scf
+ * (prec/mixed_tol/switch_tol as there; incremental builds, graph and
+ * guess_fallback are not used).
+ * P_in: device 4 x nbf^2 c128 Hermitian Pauli components (NULL: core guess,
+ * which is collinear); P_out (required), F_out (may be NULL): device
+ * 4 x nbf^2 c128.  Returns CQ_ERR_NOT_CONVERGED (stats filled) if max_iter
+ * is reached.  Synchronises `stream` every iteration. */
+int cq_scf_ghf(cq_basis* b, int nelec, const cq_scf_opts* opts, const void* P_in,
+               void* P_out, void* F_out, cq_scf_stats* stats, void* stream);
 
 /* Batched RHF SCF over the molecules of a batched basis
  * (cq_basis_create_batch): one Fock build for all molecules per iteration,
@@ -267,7 +287,10 @@ int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
  * flags) lives on the device, so with opts->graph the iterations after the
  * first are captured once as a CUDA graph and replayed; the host reads the
  * number of open molecules one iteration behind (at most one extra, no-op
- * iteration).  Runs on a private stream ordered after `stream`; returns
+ * iteration).  With D_in and opts->guess_fallback = k > 1, a molecule not
+ * converged after k iterations restarts from the core-Hamiltonian guess
+ * (the supplied guess is then only a first try; the answer is judged by
+ * the SCF either way).  Runs on a private stream ordered after `stream`; returns
  * after it has drained.  Returns CQ_ERR_NOT_CONVERGED if any molecule
  * reached max_iter.  stats->iterations is the number of batched iterations,
  * stats->converged the number of converged molecules, stats->energy the sum

@@ -40,7 +40,7 @@ class SCFOpts(ctypes.Structure):
     _fields_ = [("e_tol", ctypes.c_double), ("d_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("prec", ctypes.c_int), ("mixed_tol", ctypes.c_double),
                 ("schwarz_tol", ctypes.c_double), ("incremental", ctypes.c_int), ("full_every", ctypes.c_int),
-                ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int)]
+                ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int), ("guess_fallback", ctypes.c_int)]
 
 
 class SCFStats(ctypes.Structure):
@@ -90,6 +90,8 @@ def lib():
         L.cq_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, dp, vp]
         L.cq_one_electron.argtypes = [vp, vp, vp, vp, vp, dp, vp]
         L.cq_scf.argtypes = [vp, ctypes.c_int, ctypes.POINTER(SCFOpts), vp, vp, vp, ctypes.POINTER(SCFStats), vp]
+        L.cq_scf_ghf.argtypes = [vp, ctypes.c_int, ctypes.POINTER(SCFOpts), vp, vp, vp, ctypes.POINTER(SCFStats),
+                                 vp]
         L.cq_rt_step.argtypes = [vp, ctypes.POINTER(RTOpts), ctypes.c_int, vp, vp, ctypes.POINTER(RTObs), vp]
         L.cq_dense_info.argtypes = [vp, ip, ip, vp]
         L.cq_autotune.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(FockOpts), ip, dp, vp]
@@ -219,14 +221,17 @@ class Basis:
 
     def scf_batch(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
                   mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, D0=None, stream=None,
-                  raise_on_fail=True, graph=True):
-        """Batched RHF; returns (D batched tensor, energies, iterations, stats)."""
+                  raise_on_fail=True, graph=True, guess_fallback=40):
+        """Batched RHF; returns (D batched tensor, energies, iterations, stats).
+        With D0, a molecule still open after guess_fallback iterations restarts
+        from the core guess (0: never)."""
         import torch
         D = torch.empty((self.nmol, self.ld, self.ld), dtype=torch.float64, device="cuda")
         no = np.ascontiguousarray(nocc, dtype=np.int32)
         E = np.zeros(self.nmol)
         it = np.zeros(self.nmol, dtype=np.int32)
-        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, int(bool(graph)))
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, int(bool(graph)),
+                    int(guess_fallback))
         st = SCFStats()
         ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
         rc = lib().cq_scf_batch(self.h, no.ctypes.data_as(ip), ctypes.byref(o),
@@ -352,6 +357,26 @@ class Basis:
                  "last_rms": st.last_rms, "quartets_fp64": st.quartets_fp64,
                  "quartets_fp32": st.quartets_fp32, "ms": st.ms, "rc": rc}
         return D, F, stats
+
+    def scf_ghf(self, nelec, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
+                mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, P0=None, stream=None, raise_on_fail=True):
+        """Two-component GHF SCF; P0 and the returned P, F are (4, nbf, nbf)
+        complex128 Pauli components.  Returns (P, F, stats dict)."""
+        import torch
+        n = self.nbf
+        P = torch.empty((4, n, n), dtype=torch.complex128, device="cuda")
+        F = torch.empty((4, n, n), dtype=torch.complex128, device="cuda")
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, 0, 0)
+        st = SCFStats()
+        rc = lib().cq_scf_ghf(self.h, int(nelec), ctypes.byref(o),
+                              _ptr(P0.contiguous()) if P0 is not None else None, _ptr(P), _ptr(F),
+                              ctypes.byref(st), _stream_ptr(stream))
+        if raise_on_fail:
+            check(rc, "cq_scf_ghf")
+        stats = {"energy": st.energy, "iterations": st.iterations, "converged": bool(st.converged),
+                 "last_rms": st.last_rms, "quartets_fp64": st.quartets_fp64,
+                 "quartets_fp32": st.quartets_fp32, "ms": st.ms, "rc": rc}
+        return P, F, stats
 
     def rt_step(self, step, P_prev, P_cur, dt=0.05, field=(0.0, 0.0, 0.0), t_on=0.0, t_off=0.0,
                 restart_every=50, prec=CQ_PREC_FP64, mixed_tol=1e-5, schwarz_tol=1e-14, obs=True,

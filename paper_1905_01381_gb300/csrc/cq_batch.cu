@@ -97,13 +97,15 @@ __global__ void batch_fock_kernel(size_t n, const double* __restrict__ H, const 
 // Iteration state kept on the device, so that an iteration is the same
 // sequence of launches every time (and can be captured once as a graph):
 // the iteration number, the DIIS ring (insertions so far, newest slot,
-// subspace size and the slots from oldest to newest) and the number of
-// molecules still open after the iteration's convergence test.
+// subspace size and the slots from oldest to newest), the number of
+// molecules open at the start of the iteration and the number still open
+// after its convergence test.
 struct BatchState {
     int it;
     int kd;
     int slot, nvec;
     int order[BDIIS];
+    int nact;
     unsigned int nopen;
 };
 
@@ -111,28 +113,78 @@ struct BatchState {
 constexpr int MODE_FP32 = 1;
 constexpr int MODE_SKIP = 2;
 
-__global__ void batch_iter_begin_kernel(BatchState* st)
+// Start of an iteration: the open molecules, in order, become the compact
+// slots 0..nact-1 of the dense steps (one block; slots nact..kb-1 repeat a
+// valid molecule and are never written back).
+__global__ void batch_begin_kernel(int nmol, int kb, const int* __restrict__ conv, const int* __restrict__ nocc,
+                                   BatchState* st, int* __restrict__ act, int* __restrict__ nocc_c)
 {
+    __shared__ int part[1024];
+    const int per = (nmol + blockDim.x - 1) / blockDim.x;
+    const int m0 = threadIdx.x * per, m1 = min(nmol, m0 + per);
+    int c = 0;
+    for (int m = m0; m < m1; ++m) c += conv[m] ? 0 : 1;
+    part[threadIdx.x] = c;
+    __syncthreads();
     if (threadIdx.x == 0) {
+        int a = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            const int x = part[i];
+            part[i] = a;
+            a += x;
+        }
         st->it += 1;
         st->nopen = 0u;
+        st->nact = min(a, kb);
+    }
+    __syncthreads();
+    int k = part[threadIdx.x];
+    for (int m = m0; m < m1; ++m)
+        if (!conv[m]) {
+            if (k < kb) { act[k] = m; nocc_c[k] = nocc[m]; }
+            ++k;
+        }
+    __syncthreads();
+    const int na = st->nact;
+    const int dummy = na > 0 ? act[0] : 0;
+    for (int i = na + threadIdx.x; i < kb; i += blockDim.x) {
+        act[i] = dummy;
+        nocc_c[i] = nocc[dummy];
     }
 }
 
-// per open molecule (one block each): E = sum (H + F) D + Enuc; rms of E'
-__global__ void batch_energy_rms_kernel(int ld, const double* __restrict__ H, const double* __restrict__ F,
-                                        const double* __restrict__ D, const double* __restrict__ Ep,
+// dst slot k <- src slot act[k] (slot = n elements), for up to three arrays
+struct Gather3 {
+    const double* src[3];
+    double* dst[3];
+};
+__global__ void batch_gather_kernel(int kb, size_t n, const int* __restrict__ act, Gather3 g)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)kb * n) return;
+    const size_t k = i / n, r = i - k * n;
+    const size_t from = (size_t)act[k] * n + r;
+    for (int q = 0; q < 3; ++q)
+        if (g.src[q]) g.dst[q][i] = g.src[q][from];
+}
+
+// per open molecule (compact slot k, one block each): E = sum (H + F) D + Enuc
+// over its full slot; rms of its orthogonal-basis error (compact)
+__global__ void batch_energy_rms_kernel(int ld, const int* __restrict__ act, const BatchState* st,
+                                        const double* __restrict__ H, const double* __restrict__ F,
+                                        const double* __restrict__ D, const double* __restrict__ Epc,
                                         const double* __restrict__ enuc, const int* __restrict__ mol_n,
-                                        const int* __restrict__ conv, double* __restrict__ E, double* __restrict__ rms)
+                                        double* __restrict__ E, double* __restrict__ rms)
 {
     __shared__ double r0[256], r1[256];
-    const int m = blockIdx.x;
-    if (conv[m]) return;
-    const size_t slot = (size_t)ld * ld, o = (size_t)m * slot;
+    const int k = blockIdx.x;
+    if (k >= st->nact) return;
+    const int m = act[k];
+    const size_t slot = (size_t)ld * ld, o = (size_t)m * slot, oc = (size_t)k * slot;
     double e = 0.0, q = 0.0;
     for (size_t i = threadIdx.x; i < slot; i += blockDim.x) {
         e += (H[o + i] + F[o + i]) * D[o + i];
-        q += Ep[o + i] * Ep[o + i];
+        q += Epc[oc + i] * Epc[oc + i];
     }
     r0[threadIdx.x] = e;
     r1[threadIdx.x] = q;
@@ -162,16 +214,20 @@ __global__ void batch_antisym_kernel(int nmol, int ld, const double* __restrict_
 // from the second iteration on, and only on an energy from an all-FP64
 // build; a molecule built in mixed precision moves to FP64 builds once its
 // orthogonal-basis error falls below switch_tol.  A converged molecule is
-// skipped by later builds; the open count goes to the state and to the
-// host-visible history (one entry per iteration).
+// skipped by later builds and dense steps; the open count goes to the state
+// and to the host-visible history (one entry per iteration).  A molecule
+// still open at iteration restart_iter (> 0) restarts from the fallback
+// density: the flag is read by the DIIS solve (fresh subspace) and the
+// density update.
 __global__ void batch_conv_kernel(int nmol, const double* __restrict__ E, const double* __restrict__ Eold,
                                   const double* __restrict__ rms, double e_tol, double d_tol, double switch_tol,
-                                  int* __restrict__ conv, int* __restrict__ iters, int* __restrict__ mode,
-                                  BatchState* st)
+                                  int restart_iter, int mode0, int* __restrict__ conv, int* __restrict__ iters,
+                                  int* __restrict__ mode, int* __restrict__ restart, BatchState* st)
 {
     const int m = blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= nmol || conv[m]) return;
     const int it = st->it;
+    restart[m] = 0;
     const int md = mode[m];
     if (it > 1 && !(md & MODE_FP32) && fabs(E[m] - Eold[m]) < e_tol && rms[m] < d_tol) {
         conv[m] = 1;
@@ -179,7 +235,12 @@ __global__ void batch_conv_kernel(int nmol, const double* __restrict__ E, const 
         mode[m] = md | MODE_SKIP;
         return;
     }
-    if ((md & MODE_FP32) && rms[m] < switch_tol) mode[m] = md & ~MODE_FP32;
+    if (it == restart_iter) {
+        restart[m] = 1;
+        mode[m] = mode0;
+    } else if ((md & MODE_FP32) && rms[m] < switch_tol) {
+        mode[m] = md & ~MODE_FP32;
+    }
     atomicAdd(&st->nopen, 1u);
 }
 
@@ -205,26 +266,31 @@ struct SlotPtrs {
     double* p[BDIIS];
 };
 
-// F and E' of the open molecules into the newest ring slot
-__global__ void batch_store_slot_kernel(int nmol, int ld, SlotPtrs Fs, SlotPtrs Es, const BatchState* st,
-                                        const int* __restrict__ conv, const double* __restrict__ F,
-                                        const double* __restrict__ Ep)
+// F and E' of the open molecules (compact slots) into the newest ring slot
+// (ring kept per molecule)
+__global__ void batch_store_slot_kernel(int kb, int ld, SlotPtrs Fs, SlotPtrs Es, const BatchState* st,
+                                        const int* __restrict__ act, const double* __restrict__ Fc,
+                                        const double* __restrict__ Epc)
 {
     const size_t slot = (size_t)ld * ld;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= slot * nmol || conv[i / slot]) return;
-    const int k = st->slot;
-    Fs.p[k][i] = F[i];
-    Es.p[k][i] = Ep[i];
+    if (i >= slot * kb) return;
+    const size_t k = i / slot, r = i - k * slot;
+    if ((int)k >= st->nact) return;
+    const size_t to = (size_t)act[k] * slot + r;
+    const int q = st->slot;
+    Fs.p[q][to] = Fc[i];
+    Es.p[q][to] = Epc[i];
 }
 
-// B[m][slot][k] = e_slot . e_k for the ring slots k (grid: molecules x BDIIS)
-__global__ void batch_dot_kernel(int ld, SlotPtrs Es, const BatchState* st, const int* __restrict__ conv,
+// B[m][slot][j] = e_slot . e_j for the ring slots j (grid: compact slots x BDIIS)
+__global__ void batch_dot_kernel(int ld, SlotPtrs Es, const BatchState* st, const int* __restrict__ act,
                                  double* __restrict__ Bm)
 {
     __shared__ double red[256];
-    const int m = blockIdx.x, p = blockIdx.y;
-    if (p >= st->nvec || conv[m]) return;
+    const int k = blockIdx.x, p = blockIdx.y;
+    if (k >= st->nact || p >= st->nvec) return;
+    const int m = act[k];
     const int pi = st->slot, pj = st->order[p];
     const size_t slot = (size_t)ld * ld, o = (size_t)m * slot;
     const double* a = Es.p[pi] + o;
@@ -233,8 +299,8 @@ __global__ void batch_dot_kernel(int ld, SlotPtrs Es, const BatchState* st, cons
     for (size_t i = threadIdx.x; i < slot; i += blockDim.x) s += a[i] * b[i];
     red[threadIdx.x] = s;
     __syncthreads();
-    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
-        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+    for (int q = blockDim.x / 2; q > 0; q >>= 1) {
+        if ((int)threadIdx.x < q) red[threadIdx.x] += red[threadIdx.x + q];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -243,16 +309,25 @@ __global__ void batch_dot_kernel(int ld, SlotPtrs Es, const BatchState* st, cons
     }
 }
 
-// Per open molecule: the DIIS coefficients over the ring slots (oldest to
-// newest) from the bordered system [B -1; -1 0][c; l] = [0; -1], by
-// Gaussian elimination with partial pivoting; one vector gives c = 1.
+// Per open molecule: the DIIS coefficients over its newest nv ring slots
+// (nv = its insertions since its last restart, at most the ring's size) from
+// the bordered system [B -1; -1 0][c; l] = [0; -1], by Gaussian elimination
+// with partial pivoting; one vector gives c = 1.  nv is kept in kdm.
 __global__ void batch_diis_solve_kernel(int nmol, const BatchState* st, const int* __restrict__ conv,
+                                        const int* __restrict__ restart, int* __restrict__ kdm,
                                         const double* __restrict__ Bm, double* __restrict__ coef)
 {
     const int mol = blockIdx.x * blockDim.x + threadIdx.x;
     if (mol >= nmol || conv[mol]) return;
-    const int m = st->nvec, N = m + 1;
     double* c = coef + (size_t)mol * BDIIS;
+    if (restart[mol]) {   // this iteration's density is replaced: start a fresh subspace
+        kdm[mol] = 0;
+        c[0] = 1.0;
+        return;
+    }
+    const int m = min(kdm[mol] + 1, st->nvec), N = m + 1;
+    kdm[mol] = m;
+    const int off = st->nvec - m;
     if (m < 2) {
         c[0] = 1.0;
         return;
@@ -260,7 +335,7 @@ __global__ void batch_diis_solve_kernel(int nmol, const BatchState* st, const in
     double A[BDIIS + 1][BDIIS + 2];
     const double* B = Bm + (size_t)mol * BDIIS * BDIIS;
     for (int i = 0; i < m; ++i) {
-        for (int j = 0; j < m; ++j) A[i][j] = B[st->order[i] * BDIIS + st->order[j]];
+        for (int j = 0; j < m; ++j) A[i][j] = B[st->order[off + i] * BDIIS + st->order[off + j]];
         A[i][m] = -1.0;
         A[i][m + 1] = 0.0;
     }
@@ -291,23 +366,27 @@ __global__ void batch_diis_solve_kernel(int nmol, const BatchState* st, const in
     for (int i = 0; i < m; ++i) c[i] = x[i];
 }
 
-// extrapolated Fock matrices (a converged molecule, whose build was
-// skipped, takes its current F so that its slot stays finite)
-__global__ void batch_diis_combine_kernel(int nmol, int ld, SlotPtrs F, const BatchState* st,
-                                          const int* __restrict__ conv, const double* __restrict__ coef,
-                                          const double* __restrict__ Fcur, double* __restrict__ out)
+// extrapolated Fock matrices of the compact slots (a molecule that has just
+// converged, restarts or fills a padding slot takes its current F)
+__global__ void batch_diis_combine_kernel(int kb, int ld, SlotPtrs F, const BatchState* st,
+                                          const int* __restrict__ act, const int* __restrict__ conv,
+                                          const int* __restrict__ kdm, const double* __restrict__ coef,
+                                          const double* __restrict__ Fc, double* __restrict__ out)
 {
     const size_t slot = (size_t)ld * ld;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= slot * nmol) return;
-    const int m = (int)(i / slot);
-    if (conv[m]) {
-        out[i] = Fcur[i];
+    if (i >= slot * kb) return;
+    const size_t k = i / slot, r = i - k * slot;
+    const int m = act[k];
+    const int nv = kdm[m];
+    if ((int)k >= st->nact || conv[m] || nv < 1) {
+        out[i] = Fc[i];
         return;
     }
-    const int nvec = st->nvec;
+    const int off = st->nvec - nv;
+    const size_t from = (size_t)m * slot + r;
     double s = 0.0;
-    for (int k = 0; k < nvec; ++k) s += coef[(size_t)m * BDIIS + k] * F.p[st->order[k]][i];
+    for (int q = 0; q < nv; ++q) s += coef[(size_t)m * BDIIS + q] * F.p[st->order[off + q]][from];
     out[i] = s;
 }
 
@@ -317,7 +396,7 @@ __global__ void fill_int_kernel(int n, int v, int* __restrict__ x)
     if (i < n) x[i] = v;
 }
 
-// keep the first nocc[m] columns of C (the occupied orbitals)
+// keep the first nocc[k] columns of C (the occupied orbitals)
 __global__ void occ_mask_kernel(int nmol, int ld, const int* __restrict__ nocc, double* __restrict__ C)
 {
     const size_t slot = (size_t)ld * ld;
@@ -327,14 +406,23 @@ __global__ void occ_mask_kernel(int nmol, int ld, const int* __restrict__ nocc, 
     if (c >= nocc[m]) C[i] = 0.0;
 }
 
-// D <- Dnew for molecules still iterating
-__global__ void freeze_update_kernel(int nmol, int ld, const int* __restrict__ conv, const double* __restrict__ Dnew,
-                                     double* __restrict__ D)
+// dst slot act[k] <- the new density of compact slot k, for the molecules
+// still open (the fallback density for a molecule restarting this
+// iteration); conv and restart may be NULL (every slot taken)
+__global__ void batch_scatter_kernel(int kb, int ld, const int* __restrict__ act, const BatchState* st,
+                                     const int* __restrict__ conv, const int* __restrict__ restart,
+                                     const double* __restrict__ Dnc, const double* __restrict__ Dfall,
+                                     double* __restrict__ dst)
 {
     const size_t slot = (size_t)ld * ld;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= slot * nmol) return;
-    if (!conv[i / slot]) D[i] = Dnew[i];
+    if (i >= slot * kb) return;
+    const size_t k = i / slot, r = i - k * slot;
+    if ((int)k >= st->nact) return;
+    const int m = act[k];
+    if (conv && conv[m]) return;
+    const size_t to = (size_t)m * slot + r;
+    dst[to] = (restart && restart[m]) ? Dfall[to] : Dnc[i];
 }
 
 static int nb256(size_t n) { return (int)((n + 255) / 256); }
@@ -347,8 +435,10 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
                             double* E_out, int* iters_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !nocc || !D_out) { set_error("cq_scf_batch: NULL argument"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 1};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 1, 0};
     if (opts) o = *opts;
+    // the core-guess fallback applies to a supplied starting density only
+    const int restart_iter = (D_in && o.guess_fallback > 1) ? o.guess_fallback : 0;
     if (o.diis_size < 1 || o.diis_size > BDIIS || o.max_iter <= 0) {
         set_error("cq_scf_batch: diis_size must be 1..8 and max_iter > 0");
         return CQ_ERR_INVALID_ARG;
@@ -389,6 +479,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     CQ_BLAS_B(cublasSetStream(blas, s));
     CQ_SOLVER_B(cusolverDnSetStream(sol, s));
     const size_t ms = (size_t)b->mstride;
+    const size_t slot = (size_t)ld * ld;
     const int ds = o.diis_size;
     std::vector<void*> bufs;
     int rc = CQ_OK;
@@ -397,9 +488,12 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
         if (!r) bufs.push_back((void*)*p);
         return r;
     };
-    double *S, *T, *V, *H, *X, *shift, *w, *D, *Dn, *J, *K, *F, *T1, *T2, *Err, *Ep, *Fd, *Bm, *coef, *E, *Eold,
-        *rms, *enuc;
-    int *conv, *iters, *d_nocc, *info, *mode;
+    // per molecule (slot = molecule): one-electron data, X, shift, density,
+    // J/K/F, DIIS ring, scalars; compact (slot k = k-th open molecule): the
+    // dense steps' operands
+    double *S, *T, *V, *H, *X, *shift, *D, *J, *K, *F, *Bm, *coef, *E, *Eold, *rms, *enuc, *Dcore = nullptr;
+    double *Fc, *Dc, *Sc, *Xc, *shc, *T1, *T2, *Epc, *Fdc, *Dnc, *w;
+    int *conv, *iters, *d_nocc, *info, *mode, *kdm, *restart, *act, *nocc_c;
     unsigned long long* acc;
     BatchState* bst;
     SlotPtrs Fs{}, Es{};
@@ -408,14 +502,18 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     std::vector<char> hwork;
     unsigned int* open_hist = nullptr;   // mapped host memory, one entry per iteration
     unsigned int* open_dev = nullptr;
-    cudaGraphExec_t gx_full = nullptr, gx_a = nullptr, gx_b = nullptr;
+    struct Graphs {
+        int kb;
+        cudaGraphExec_t full, a, b;
+    };
+    std::vector<Graphs> graphs;
     cudaEvent_t iev[2] = {nullptr, nullptr}, e0 = nullptr, e1 = nullptr;
     const int hist_len = o.max_iter + 2;
     auto fail = [&](int r) {
         if (r != CQ_OK) cudaStreamSynchronize(s);
-        if (gx_full) cudaGraphExecDestroy(gx_full);
-        if (gx_a) cudaGraphExecDestroy(gx_a);
-        if (gx_b) cudaGraphExecDestroy(gx_b);
+        for (Graphs& g : graphs)
+            for (cudaGraphExec_t x : {g.full, g.a, g.b})
+                if (x) cudaGraphExecDestroy(x);
         for (cudaEvent_t e : {iev[0], iev[1], e0, e1})
             if (e) cudaEventDestroy(e);
         if (prm) cusolverDnDestroyParams(prm);
@@ -426,13 +524,15 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     };
 #define GETB(p, n)                          \
     if ((rc = get(&(p), (n)))) return fail(rc);
-    GETB(S, ms) GETB(T, ms) GETB(V, ms) GETB(H, ms) GETB(X, ms) GETB(shift, (size_t)nmol * ld) GETB(w, (size_t)nmol * ld)
-    GETB(D, ms) GETB(Dn, ms) GETB(J, ms) GETB(K, ms) GETB(F, ms) GETB(T1, ms) GETB(T2, ms) GETB(Err, ms) GETB(Ep, ms)
-    GETB(Fd, ms) GETB(Bm, (size_t)nmol * BDIIS * BDIIS) GETB(coef, (size_t)nmol * BDIIS) GETB(E, nmol) GETB(Eold, nmol)
-    GETB(rms, nmol) GETB(enuc, nmol)
+    GETB(S, ms) GETB(T, ms) GETB(V, ms) GETB(H, ms) GETB(X, ms) GETB(shift, (size_t)nmol * ld) GETB(D, ms)
+    GETB(J, ms) GETB(K, ms) GETB(F, ms) GETB(Bm, (size_t)nmol * BDIIS * BDIIS) GETB(coef, (size_t)nmol * BDIIS)
+    GETB(E, nmol) GETB(Eold, nmol) GETB(rms, nmol) GETB(enuc, nmol)
+    GETB(Fc, ms) GETB(Dc, ms) GETB(Sc, ms) GETB(Xc, ms) GETB(shc, (size_t)nmol * ld) GETB(T1, ms) GETB(T2, ms)
+    GETB(Epc, ms) GETB(Fdc, ms) GETB(Dnc, ms) GETB(w, (size_t)nmol * ld)
     for (int k = 0; k < ds; ++k) { GETB(Fs.p[k], ms) GETB(Es.p[k], ms) }
     GETB(conv, nmol) GETB(iters, nmol) GETB(d_nocc, nmol) GETB(info, nmol) GETB(mode, nmol) GETB(acc, 4)
-    GETB(bst, 1)
+    GETB(bst, 1) GETB(kdm, nmol) GETB(restart, nmol) GETB(act, nmol) GETB(nocc_c, nmol)
+    if (restart_iter) GETB(Dcore, ms)
 #undef GETB
     if (cudaHostAlloc((void**)&open_hist, hist_len * sizeof(unsigned int), cudaHostAllocMapped) != cudaSuccess ||
         cudaHostGetDevicePointer((void**)&open_dev, open_hist, 0) != cudaSuccess) {
@@ -464,84 +564,110 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     }
     if (cudaMalloc(&dwork, dws > 0 ? dws : 1) != cudaSuccess) { set_error("cq_scf_batch: OOM"); return fail(CQ_ERR_OOM); }
     hwork.resize(hws > 0 ? hws : 1);
-    auto eig = [&](double* A) -> int {
+    // eigenpairs of the first kb slots of A (the workspace is sized for nmol)
+    auto eig = [&](double* A, int kb) -> int {
         if (cusolverDnXsyevBatched(sol, prm, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, ld, CUDA_R_64F, A, ld,
                                    CUDA_R_64F, w, CUDA_R_64F, dwork, dws, hwork.data(), hws, info,
-                                   nmol) != CUSOLVER_STATUS_SUCCESS) {
+                                   kb) != CUSOLVER_STATUS_SUCCESS) {
             set_error("cusolverDnXsyevBatched failed");
             return CQ_ERR_CUDA;
         }
         return CQ_OK;
     };
     pad_overlap_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, b->d_mol_n, S, T1);
-    if ((rc = eig(T1))) return fail(rc);
+    if ((rc = eig(T1, nmol))) return fail(rc);
     batch_ortho_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, T1, w, X, shift);
-    // orthogonal-basis Fock matrix X^T F X, shifted, into T2 (diagonalised in place)
-    auto ortho_fock = [&](const double* Fm) -> int {
-        CQ_BLAS_B(gemm_batch(blas, true, false, ld, nmol, 1.0, X, Fm, 0.0, T1));
-        CQ_BLAS_B(gemm_batch(blas, false, false, ld, nmol, 1.0, T1, X, 0.0, T2));
-        add_diag_kernel<<<nb256((size_t)nmol * ld), 256, 0, s>>>(nmol, ld, shift, T2);
+    auto gather = [&](int kb, size_t n, const double* s0, double* d0, const double* s1, double* d1,
+                      const double* s2, double* d2) {
+        Gather3 g{{s0, s1, s2}, {d0, d1, d2}};
+        batch_gather_kernel<<<nb256((size_t)kb * n), 256, 0, s>>>(kb, n, act, g);
+    };
+    // orthogonal-basis Fock matrices Xc^T Fm Xc of the compact slots, shifted, into T2
+    auto ortho_fock = [&](int kb, const double* Fm) -> int {
+        CQ_BLAS_B(gemm_batch(blas, true, false, ld, kb, 1.0, Xc, Fm, 0.0, T1));
+        CQ_BLAS_B(gemm_batch(blas, false, false, ld, kb, 1.0, T1, Xc, 0.0, T2));
+        add_diag_kernel<<<nb256((size_t)kb * ld), 256, 0, s>>>(kb, ld, shc, T2);
         return CQ_OK;
     };
-    // rows of T2 are eigenvectors: C = X T2^T, occupied columns kept,
-    // D = C C^T taken by the molecules still open
-    auto new_density = [&]() -> int {
-        CQ_BLAS_B(gemm_batch(blas, false, true, ld, nmol, 1.0, X, T2, 0.0, T1));
-        occ_mask_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, d_nocc, T1);
-        CQ_BLAS_B(gemm_batch(blas, false, true, ld, nmol, 1.0, T1, T1, 0.0, Dn));
-        freeze_update_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, conv, Dn, D);
-        return cudaGetLastError() == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
+    // rows of T2 are eigenvectors: C = Xc T2^T, occupied columns kept, Dnc = C C^T
+    auto density_c = [&](int kb) -> int {
+        CQ_BLAS_B(gemm_batch(blas, false, true, ld, kb, 1.0, Xc, T2, 0.0, T1));
+        occ_mask_kernel<<<nb256((size_t)kb * slot), 256, 0, s>>>(kb, ld, nocc_c, T1);
+        CQ_BLAS_B(gemm_batch(blas, false, true, ld, kb, 1.0, T1, T1, 0.0, Dnc));
+        return CQ_OK;
     };
     if (cudaMemsetAsync(conv, 0, nmol * sizeof(int), s) || cudaMemsetAsync(iters, 0, nmol * sizeof(int), s) ||
         cudaMemsetAsync(Eold, 0, nmol * sizeof(double), s) || cudaMemsetAsync(E, 0, nmol * sizeof(double), s) ||
-        cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), s) || cudaMemsetAsync(bst, 0, sizeof(BatchState), s))
+        cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), s) || cudaMemsetAsync(bst, 0, sizeof(BatchState), s) ||
+        cudaMemsetAsync(kdm, 0, nmol * sizeof(int), s) || cudaMemsetAsync(restart, 0, nmol * sizeof(int), s))
         return fail(CQ_ERR_CUDA);
-    fill_int_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, o.prec == CQ_PREC_MIXED ? MODE_FP32 : 0, mode);
+    const int mode0 = o.prec == CQ_PREC_MIXED ? MODE_FP32 : 0;
+    fill_int_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, mode0, mode);
+    // core-guess density of every molecule into dst (the starting density, or
+    // the fallback of a supplied one)
+    auto core_guess = [&](double* dst) -> int {
+        batch_begin_kernel<<<1, 1024, 0, s>>>(nmol, nmol, conv, d_nocc, bst, act, nocc_c);
+        gather(nmol, slot, H, Fdc, X, Xc, nullptr, nullptr);
+        gather(nmol, ld, shift, shc, nullptr, nullptr, nullptr, nullptr);
+        int r;
+        if ((r = ortho_fock(nmol, Fdc)) || (r = eig(T2, nmol)) || (r = density_c(nmol))) return r;
+        batch_scatter_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, act, bst, nullptr, nullptr, Dnc, nullptr, dst);
+        return cudaGetLastError() == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
+    };
+    if (restart_iter && (rc = core_guess(Dcore))) return fail(rc);
     if (D_in) {
         if (cudaMemcpyAsync(D, D_in, ms * sizeof(double), cudaMemcpyDeviceToDevice, s)) return fail(CQ_ERR_CUDA);
-    } else {
-        if ((rc = ortho_fock(H)) || (rc = eig(T2)) || (rc = new_density())) return fail(rc);
+    } else if ((rc = core_guess(D))) {
+        return fail(rc);
     }
-    // Phase A of an iteration: Fock build for the open molecules, energy,
-    // orthogonal-basis error, convergence test, DIIS extrapolation (not on
-    // the first iteration from a supplied density, which need not be
-    // idempotent), X^T F X.  Then the eigensolver, then phase B (density).
-    auto phase_a = [&](bool first) -> int {
-        batch_iter_begin_kernel<<<1, 32, 0, s>>>(bst);
+    // the set-up passes above advanced the iteration counter
+    if (cudaMemsetAsync(bst, 0, sizeof(BatchState), s)) return fail(CQ_ERR_CUDA);
+    // Phase A of an iteration over kb compact slots (kb >= open molecules):
+    // compaction, Fock build for the open molecules, energy, orthogonal-basis
+    // error, convergence test, DIIS extrapolation (not on the first iteration
+    // from a supplied density, which need not be idempotent), Xc^T F Xc.  Then
+    // the eigensolver, then phase B (density, written back per molecule).
+    auto phase_a = [&](int kb, bool first) -> int {
+        batch_begin_kernel<<<1, 1024, 0, s>>>(nmol, kb, conv, d_nocc, bst, act, nocc_c);
         cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, o.prec, 1, 1};
         int r = fock_build_modes(b, CQ_DENS_REAL_SYM, D, J, K, &fo, nullptr, s, mode, acc);
         if (r) return r;
         batch_fock_kernel<<<nb256(ms), 256, 0, s>>>(ms, H, J, K, F);
-        CQ_BLAS_B(gemm_batch(blas, false, false, ld, nmol, 1.0, F, D, 0.0, T1));
-        CQ_BLAS_B(gemm_batch(blas, false, false, ld, nmol, 1.0, T1, S, 0.0, T2));
-        batch_antisym_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, T2, Err);
-        CQ_BLAS_B(gemm_batch(blas, true, false, ld, nmol, 1.0, X, Err, 0.0, T1));
-        CQ_BLAS_B(gemm_batch(blas, false, false, ld, nmol, 1.0, T1, X, 0.0, Ep));
-        batch_energy_rms_kernel<<<nmol, 256, 0, s>>>(ld, H, F, D, Ep, enuc, b->d_mol_n, conv, E, rms);
-        batch_conv_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, E, Eold, rms, o.e_tol, o.d_tol, o.switch_tol, conv,
-                                                             iters, mode, bst);
+        const size_t nc = (size_t)kb * slot;
+        gather(kb, slot, F, Fc, D, Dc, S, Sc);
+        gather(kb, slot, X, Xc, nullptr, nullptr, nullptr, nullptr);
+        gather(kb, ld, shift, shc, nullptr, nullptr, nullptr, nullptr);
+        CQ_BLAS_B(gemm_batch(blas, false, false, ld, kb, 1.0, Fc, Dc, 0.0, T1));
+        CQ_BLAS_B(gemm_batch(blas, false, false, ld, kb, 1.0, T1, Sc, 0.0, T2));
+        batch_antisym_kernel<<<nb256(nc), 256, 0, s>>>(kb, ld, T2, Fdc);
+        CQ_BLAS_B(gemm_batch(blas, true, false, ld, kb, 1.0, Xc, Fdc, 0.0, T1));
+        CQ_BLAS_B(gemm_batch(blas, false, false, ld, kb, 1.0, T1, Xc, 0.0, Epc));
+        batch_energy_rms_kernel<<<kb, 256, 0, s>>>(ld, act, bst, H, F, D, Epc, enuc, b->d_mol_n, E, rms);
+        batch_conv_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, E, Eold, rms, o.e_tol, o.d_tol, o.switch_tol,
+                                                             restart_iter, mode0, conv, iters, mode, restart, bst);
         batch_publish_kernel<<<1, 32, 0, s>>>(bst, open_dev, hist_len);
         if (cudaMemcpyAsync(Eold, E, nmol * sizeof(double), cudaMemcpyDeviceToDevice, s)) return CQ_ERR_CUDA;
-        const double* Fuse = F;
+        const double* Fuse = Fc;
         if (!first) {
             batch_diis_index_kernel<<<1, 32, 0, s>>>(bst, ds);
-            batch_store_slot_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, Fs, Es, bst, conv, F, Ep);
-            batch_dot_kernel<<<dim3(nmol, BDIIS), 256, 0, s>>>(ld, Es, bst, conv, Bm);
-            batch_diis_solve_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, bst, conv, Bm, coef);
-            batch_diis_combine_kernel<<<nb256(ms), 256, 0, s>>>(nmol, ld, Fs, bst, conv, coef, F, Fd);
-            Fuse = Fd;
+            batch_store_slot_kernel<<<nb256(nc), 256, 0, s>>>(kb, ld, Fs, Es, bst, act, Fc, Epc);
+            batch_dot_kernel<<<dim3(kb, BDIIS), 256, 0, s>>>(ld, Es, bst, act, Bm);
+            batch_diis_solve_kernel<<<(nmol + 127) / 128, 128, 0, s>>>(nmol, bst, conv, restart, kdm, Bm, coef);
+            batch_diis_combine_kernel<<<nb256(nc), 256, 0, s>>>(kb, ld, Fs, bst, act, conv, kdm, coef, Fc, Fdc);
+            Fuse = Fdc;
         }
-        if ((r = ortho_fock(Fuse))) return r;
+        if ((r = ortho_fock(kb, Fuse))) return r;
         return cudaGetLastError() == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
     };
-    auto whole = [&]() -> int {
-        int r = phase_a(false);
-        if (!r) r = eig(T2);
-        if (!r) r = new_density();
-        return r;
+    auto phase_b = [&](int kb) -> int {
+        int r = density_c(kb);
+        if (r) return r;
+        batch_scatter_kernel<<<nb256((size_t)kb * slot), 256, 0, s>>>(kb, ld, act, bst, conv, restart, Dnc, Dcore, D);
+        return cudaGetLastError() == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
     };
     auto capture = [&](auto&& fn, cudaGraphExec_t* out) -> bool {
         cudaGraph_t g = nullptr;
+        *out = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
             cudaGetLastError();
             return false;
@@ -552,48 +678,72 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
         if (ok && cudaGraphInstantiate(out, g, 0) != cudaSuccess) ok = false;
         if (g) cudaGraphDestroy(g);
         if (!ok) {
+            if (*out) cudaGraphExecDestroy(*out);
             *out = nullptr;
             cudaGetLastError();
         }
         return ok;
     };
-    int graph_used = 0;
-    auto run_iter = [&](bool first) -> int {
-        if (gx_full) return cudaGraphLaunch(gx_full, s) == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
-        int r;
-        if (gx_a) {
-            if (cudaGraphLaunch(gx_a, s) != cudaSuccess) return CQ_ERR_CUDA;
-            if ((r = eig(T2))) return r;
-            return cudaGraphLaunch(gx_b, s) == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
-        }
-        if ((r = phase_a(first)) || (r = eig(T2))) return r;
-        return new_density();
-    };
-    // Iteration 1 runs eagerly (it also sizes the build's scratch); the
-    // later iterations are one launch sequence, captured once as a graph
-    // (the eigensolver left outside it if it cannot be captured) and
-    // replayed.  The host reads the open count of iteration k-1 while
-    // iteration k runs; iterations after the last molecule converged skip
-    // every quartet and leave every density as it is.
-    cudaEventRecord(e0, s);
-    int done = 0;
-    for (int it = 1; it <= o.max_iter; ++it) {
-        if (it == 2 && o.graph && !b->profile) {
-            if (capture(whole, &gx_full)) {
-                graph_used = 2;
-            } else if (capture([&]() { return phase_a(false); }, &gx_a) && capture(new_density, &gx_b)) {
-                graph_used = 1;
-            } else {
-                if (gx_a) cudaGraphExecDestroy(gx_a);
-                gx_a = nullptr;
+    // graphs per compact size kb, captured on first use: the whole iteration
+    // (level 2) or the two phases around an eager eigensolver call (level 1)
+    int graph_level = o.graph && !b->profile ? 2 : 0;
+    auto graphs_for = [&](int kb) -> Graphs* {
+        for (Graphs& g : graphs)
+            if (g.kb == kb) return &g;
+        Graphs g{kb, nullptr, nullptr, nullptr};
+        if (graph_level == 2 &&
+            !capture([&]() {
+                int r = phase_a(kb, false);
+                if (!r) r = eig(T2, kb);
+                if (!r) r = phase_b(kb);
+                return r;
+            }, &g.full))
+            graph_level = 1;
+        if (graph_level == 1 && !g.full) {
+            if (!capture([&]() { return phase_a(kb, false); }, &g.a) || !capture([&]() { return phase_b(kb); }, &g.b)) {
+                if (g.a) cudaGraphExecDestroy(g.a);
+                g.a = nullptr;
+                graph_level = 0;
             }
         }
-        if ((rc = run_iter(it == 1 && D_in != nullptr))) return fail(rc);
+        graphs.push_back(g);
+        return &graphs.back();
+    };
+    auto run_iter = [&](int kb, bool first, bool eager) -> int {
+        Graphs* g = eager || graph_level == 0 ? nullptr : graphs_for(kb);
+        if (g && g->full) return cudaGraphLaunch(g->full, s) == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
+        int r;
+        if (g && g->a) {
+            if (cudaGraphLaunch(g->a, s) != cudaSuccess) return CQ_ERR_CUDA;
+            if ((r = eig(T2, kb))) return r;
+            return cudaGraphLaunch(g->b, s) == cudaSuccess ? CQ_OK : CQ_ERR_CUDA;
+        }
+        if ((r = phase_a(kb, first)) || (r = eig(T2, kb))) return r;
+        return phase_b(kb);
+    };
+    // compact size for a known number of open molecules: the next power of
+    // two, at most nmol (so a handful of graphs covers the whole run)
+    auto bucket = [&](int open) {
+        int kb = 1;
+        while (kb < open) kb <<= 1;
+        return kb < nmol ? kb : nmol;
+    };
+    // Iteration 1 runs eagerly (it also sizes the build's scratch); later
+    // iterations replay the graph of their compact size.  The host reads the
+    // open count of iteration k-1 while iteration k runs (so the compact size
+    // of iteration k+1 bounds its open molecules); iterations after the last
+    // molecule converged skip every quartet and every dense step.
+    cudaEventRecord(e0, s);
+    int done = 0, known_open = nmol;
+    for (int it = 1; it <= o.max_iter; ++it) {
+        const int kb = bucket(known_open);
+        if ((rc = run_iter(kb, it == 1 && D_in != nullptr, it == 1))) return fail(rc);
         if (cudaEventRecord(iev[it & 1], s) != cudaSuccess) return fail(CQ_ERR_CUDA);
         done = it;
         if (it >= 2) {
             if (cudaEventSynchronize(iev[(it - 1) & 1]) != cudaSuccess) return fail(CQ_ERR_CUDA);
-            if (open_hist[it - 1] == 0u) {
+            known_open = (int)open_hist[it - 1];
+            if (known_open == 0) {
                 done = it - 1;
                 break;
             }
@@ -627,7 +777,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     st.quartets_fp64 = hacc[0];
     st.quartets_fp32 = hacc[2];
     st.ms = msf;
-    st.graph = graph_used;
+    st.graph = o.graph && !b->profile ? graph_level : 0;
     if (stats) *stats = st;
     fail(CQ_OK);
     if (nconv < nmol) {

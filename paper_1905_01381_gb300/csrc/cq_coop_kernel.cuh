@@ -38,7 +38,9 @@ __device__ __forceinline__ int coop_node(int shape, const int4 d, const R* __res
 }
 
 template <typename R>
-__global__ void __launch_bounds__(COOP_THREADS) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
+struct CoopMinBlocks { static constexpr int v = sizeof(R) == 4 ? 8 : 6; };
+template <typename R>
+__global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
 {
     const CoopClass C = COOP_CLASSES_D[qc];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;

@@ -351,7 +351,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
                       double* F_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !D_out) { set_error("cq_scf: NULL basis or output"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0};
     if (opts) o = *opts;
     const int n = b->nbf;
     if (b->nmol > 1) { set_error("cq_scf: batched basis; use cq_scf_batch"); return CQ_ERR_UNSUPPORTED; }
@@ -725,5 +725,268 @@ extern "C" int cq_dense_info(cq_basis* b, int* northo, int* ndropped, void* stre
     if (rc) return rc;
     if (northo) *northo = b->northo;
     if (ndropped) *ndropped = b->ndropped;
+    return CQ_OK;
+}
+
+// ------------------------------------------------------------------ GHF SCF
+// Two-component SCF in the Pauli representation (Eq. pauli_sep, Eq.
+// 2c_fock): densities P^I (I = 0..3, complex n x n), F^0 = h + 2J[P^0] -
+// K[P^0], F^k = -K[P^k]; the 2n x 2n Fock matrix sum_I sigma_I (x) F^I is
+// diagonalised in the orthonormal basis diag(X, X), the nelec lowest spinors
+// give P^{2C} = C C^+, split back into its Pauli components.  Energy
+// E = sum_I Re Tr[(h^I + F^I) P^I] + E_nuc (h^k = 0).  DIIS on the
+// orthogonal-basis commutator with real B_ij = Re <e_i|e_j>.
+namespace cq {
+
+__global__ void ghf_fock_kernel(size_t nn, const double* __restrict__ h, const double* __restrict__ J,
+                                const cuDoubleComplex* __restrict__ K, cuDoubleComplex* __restrict__ F)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nn) return;
+    F[i] = make_cuDoubleComplex(h[i] + 2.0 * J[i] - K[i].x, -K[i].y);
+    for (int k = 1; k < 4; ++k) F[k * nn + i] = make_cuDoubleComplex(-K[k * nn + i].x, -K[k * nn + i].y);
+}
+
+// out = F with h added to the scalar component (the energy's h^I + F^I)
+__global__ void ghf_hf_kernel(size_t nn, const double* __restrict__ h, const cuDoubleComplex* __restrict__ F,
+                              cuDoubleComplex* __restrict__ out)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 4 * nn) return;
+    cuDoubleComplex v = F[i];
+    if (i < nn) v.x += h[i];
+    out[i] = v;
+}
+
+// Y (2n x 2n) = sum_I sigma_I (x) X^I
+__global__ void pauli_join_kernel(int n, const cuDoubleComplex* __restrict__ X, cuDoubleComplex* __restrict__ Y)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nn) return;
+    const int i = (int)(t / n), j = (int)(t % n);
+    const cuDoubleComplex x0 = X[t], x1 = X[nn + t], x2 = X[2 * nn + t], x3 = X[3 * nn + t];
+    const size_t N = 2 * (size_t)n;
+    Y[i * N + j] = make_cuDoubleComplex(x0.x + x3.x, x0.y + x3.y);
+    Y[(n + i) * N + n + j] = make_cuDoubleComplex(x0.x - x3.x, x0.y - x3.y);
+    Y[i * N + n + j] = make_cuDoubleComplex(x1.x + x2.y, x1.y - x2.x);         // x1 - i x2
+    Y[(n + i) * N + j] = make_cuDoubleComplex(x1.x - x2.y, x1.y + x2.x);       // x1 + i x2
+}
+
+// X^0 = (aa + bb)/2, X^1 = (ab + ba)/2, X^2 = i (ab - ba)/2, X^3 = (aa - bb)/2
+__global__ void pauli_split_kernel(int n, const cuDoubleComplex* __restrict__ Y, cuDoubleComplex* __restrict__ X)
+{
+    const size_t nn = (size_t)n * n;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nn) return;
+    const int i = (int)(t / n), j = (int)(t % n);
+    const size_t N = 2 * (size_t)n;
+    const cuDoubleComplex aa = Y[i * N + j], bb = Y[(n + i) * N + n + j];
+    const cuDoubleComplex ab = Y[i * N + n + j], ba = Y[(n + i) * N + j];
+    X[t] = make_cuDoubleComplex(0.5 * (aa.x + bb.x), 0.5 * (aa.y + bb.y));
+    X[nn + t] = make_cuDoubleComplex(0.5 * (ab.x + ba.x), 0.5 * (ab.y + ba.y));
+    X[2 * nn + t] = make_cuDoubleComplex(-0.5 * (ab.y - ba.y), 0.5 * (ab.x - ba.x));
+    X[3 * nn + t] = make_cuDoubleComplex(0.5 * (aa.x - bb.x), 0.5 * (aa.y - bb.y));
+}
+
+// X2 (2n x 2m) = diag(X, X), X real n x m
+__global__ void block_diag_kernel(int n, int m, const double* __restrict__ X, cuDoubleComplex* __restrict__ X2)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)4 * n * m) return;
+    const int r = (int)(t / (2 * m)), c = (int)(t % (2 * m));
+    const bool same = (r < n) == (c < m);
+    X2[t] = make_cuDoubleComplex(same ? X[(size_t)(r % n) * m + (c % m)] : 0.0, 0.0);
+}
+
+// E = T - T^+
+__global__ void antiherm_kernel(int N, const cuDoubleComplex* __restrict__ T, cuDoubleComplex* __restrict__ E)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)N * N) return;
+    const int i = (int)(t / N), j = (int)(t % N);
+    const cuDoubleComplex a = T[t], b = T[(size_t)j * N + i];
+    E[t] = make_cuDoubleComplex(a.x - b.x, a.y + b.y);
+}
+
+}  // namespace cq
+
+extern "C" int cq_scf_ghf(cq_basis* b, int nelec, const cq_scf_opts* opts, const void* P_in, void* P_out,
+                          void* F_out, cq_scf_stats* stats, void* stream)
+{
+    if (!b || !P_out) { set_error("cq_scf_ghf: NULL basis or output"); return CQ_ERR_INVALID_ARG; }
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0};
+    if (opts) o = *opts;
+    const int n = b->nbf;
+    if (b->nmol > 1) { set_error("cq_scf_ghf: batched basis"); return CQ_ERR_UNSUPPORTED; }
+    if (nelec <= 0 || nelec > 2 * n) { set_error("cq_scf_ghf: nelec out of range"); return CQ_ERR_INVALID_ARG; }
+    if (o.max_iter <= 0 || o.diis_size < 1 || o.diis_size > DIIS_MAX) {
+        set_error("cq_scf_ghf: max_iter must be > 0 and diis_size in 1..8");
+        return CQ_ERR_INVALID_ARG;
+    }
+    if (o.prec != CQ_PREC_FP64 && o.prec != CQ_PREC_MIXED) {
+        set_error("cq_scf_ghf: unknown precision mode");
+        return CQ_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_dense(b, s);
+    if (rc) return rc;
+    const int m = b->northo;
+    if (nelec > 2 * m) { set_error("cq_scf_ghf: more electrons than spinors"); return CQ_ERR_INVALID_ARG; }
+    cublasHandle_t blas = (cublasHandle_t)b->blas;
+    cusolverDnHandle_t sol = (cusolverDnHandle_t)b->solver;
+    CQ_BLAS(cublasSetStream(blas, s));
+    CQ_SOLVER(cusolverDnSetStream(sol, s));
+    const int N = 2 * n, M = 2 * m;
+    const size_t nn = (size_t)n * n, NN = (size_t)N * N, MM = (size_t)M * M;
+    using Z = cuDoubleComplex;
+    std::vector<void*> bufs;
+    auto get = [&](auto** p, size_t cnt) -> int {
+        int r = dalloc(p, cnt);
+        if (!r) bufs.push_back((void*)*p);
+        return r;
+    };
+    Z *P, *P2, *F, *F2, *K, *X2, *S2, *T1, *T2, *Err, *Ep, *Fp, *C, *Fd, *HF, *work;
+    Z *Fs[DIIS_MAX], *Es[DIIS_MAX];
+    double *J, *w, *Bm, *coef, *scal;
+    int *slots, *info;
+    auto cleanup = [&]() {
+        for (void* p : bufs) cudaFree(p);
+    };
+    int lwork = 0;
+#define GETZ(p, c)                      \
+    if ((rc = get(&(p), (c)))) {        \
+        cleanup();                      \
+        return rc;                      \
+    }
+    GETZ(P, 4 * nn) GETZ(P2, NN) GETZ(F, 4 * nn) GETZ(F2, NN) GETZ(K, 4 * nn) GETZ(X2, (size_t)N * M) GETZ(S2, NN)
+    GETZ(T1, NN) GETZ(T2, NN) GETZ(Err, NN) GETZ(Ep, MM) GETZ(Fp, MM) GETZ(C, (size_t)N * nelec) GETZ(Fd, NN)
+    GETZ(HF, 4 * nn) GETZ(J, nn) GETZ(w, M) GETZ(Bm, DIIS_MAX * DIIS_MAX) GETZ(coef, DIIS_MAX) GETZ(scal, 4)
+    GETZ(slots, DIIS_MAX) GETZ(info, 1)
+    for (int k = 0; k < o.diis_size; ++k) { GETZ(Fs[k], NN) GETZ(Es[k], MM) }
+    if (cusolverDnZheevd_bufferSize(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, Fp, M, w, &lwork) !=
+        CUSOLVER_STATUS_SUCCESS) {
+        cleanup();
+        set_error("cusolverDnZheevd_bufferSize failed");
+        return CQ_ERR_CUDA;
+    }
+    GETZ(work, (size_t)(lwork > 0 ? lwork : 1))
+#undef GETZ
+    const Z one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    block_diag_kernel<<<nblk((size_t)N * M), 256, 0, s>>>(n, m, b->d_X, X2);
+    {   // S2 = diag(S, S) as a complex matrix: the Pauli join of (S, 0, 0, 0)
+        CQ_CUDA(cudaMemsetAsync(HF, 0, 4 * nn * sizeof(Z), s));
+        real_to_complex_kernel<<<nblk(nn), 256, 0, s>>>(nn, b->d_S, HF);
+        pauli_join_kernel<<<nblk(nn), 256, 0, s>>>(n, HF, S2);
+    }
+    // P2 from a 2n x 2n Fock matrix: Fp = X2^+ F X2, eigh, C = X2 (rows 0..nelec-1 of Fp)^+, P2 = C C^+
+    auto density_from = [&](const Z* Fm) -> int {
+        CQ_BLAS(zgemm_rm(blas, 'C', 'N', M, N, N, one, X2, M, Fm, N, zero, T1, N));
+        CQ_BLAS(zgemm_rm(blas, 'N', 'N', M, M, N, one, T1, N, X2, M, zero, Fp, M));
+        CQ_SOLVER(cusolverDnZheevd(sol, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, M, Fp, M, w, work, lwork,
+                                   info));
+        CQ_BLAS(zgemm_rm(blas, 'N', 'C', N, nelec, M, one, X2, M, Fp, M, zero, C, nelec));
+        CQ_BLAS(zgemm_rm(blas, 'N', 'C', N, N, nelec, one, C, nelec, C, nelec, zero, P2, N));
+        pauli_split_kernel<<<nblk(nn), 256, 0, s>>>(n, P2, P);
+        return CQ_OK;
+    };
+    if (P_in) {
+        CQ_CUDA(cudaMemcpyAsync(P, P_in, 4 * nn * sizeof(Z), cudaMemcpyDeviceToDevice, s));
+        pauli_join_kernel<<<nblk(nn), 256, 0, s>>>(n, P, P2);
+    } else {   // core guess: diag(h, h)
+        CQ_CUDA(cudaMemsetAsync(HF, 0, 4 * nn * sizeof(Z), s));
+        real_to_complex_kernel<<<nblk(nn), 256, 0, s>>>(nn, b->d_H, HF);
+        pauli_join_kernel<<<nblk(nn), 256, 0, s>>>(n, HF, F2);
+        if ((rc = density_from(F2))) { cleanup(); return rc; }
+    }
+    cq_scf_stats st;
+    memset(&st, 0, sizeof st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, s);
+    double Eold = 0.0, E = 0.0, rms = 0.0;
+    int nvec = 0, head = 0, it = 0;
+    bool final_fp64 = (o.prec == CQ_PREC_FP64), converged = false;
+    for (it = 1; it <= o.max_iter; ++it) {
+        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, final_fp64 ? CQ_PREC_FP64 : CQ_PREC_MIXED, 1, 1};
+        cq_fock_stats fst;
+        if ((rc = cq_fock_build(b, CQ_DENS_PAULI4, P, J, K, &fo, &fst, s))) { cleanup(); return rc; }
+        st.quartets_fp64 += fst.quartets_fp64;
+        st.quartets_fp32 += fst.quartets_fp32;
+        ghf_fock_kernel<<<nblk(nn), 256, 0, s>>>(nn, b->d_H, J, K, F);
+        ghf_hf_kernel<<<nblk(4 * nn), 256, 0, s>>>(nn, b->d_H, F, HF);
+        // Re sum (h^I + F^I)_ij conj(P^I_ij) = Re Tr[(h^I + F^I) P^I] for Hermitian P^I
+        dot_kernel<<<1, 256, 0, s>>>(8 * nn, (const double*)HF, (const double*)P, b->enuc, 1.0, 0, scal);
+        pauli_join_kernel<<<nblk(nn), 256, 0, s>>>(n, F, F2);
+        // error X2^+ (F2 P2 S2 - S2 P2 F2) X2
+        CQ_BLAS(zgemm_rm(blas, 'N', 'N', N, N, N, one, F2, N, P2, N, zero, T1, N));
+        CQ_BLAS(zgemm_rm(blas, 'N', 'N', N, N, N, one, T1, N, S2, N, zero, T2, N));
+        antiherm_kernel<<<nblk(NN), 256, 0, s>>>(N, T2, Err);
+        CQ_BLAS(zgemm_rm(blas, 'C', 'N', M, N, N, one, X2, M, Err, N, zero, T1, N));
+        CQ_BLAS(zgemm_rm(blas, 'N', 'N', M, M, N, one, T1, N, X2, M, zero, Ep, M));
+        dot_kernel<<<1, 256, 0, s>>>(2 * MM, (const double*)Ep, nullptr, 0.0, 1.0 / (double)MM, 1, scal + 1);
+        double hv[2];
+        CQ_CUDA(cudaMemcpyAsync(hv, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CQ_CUDA(cudaStreamSynchronize(s));
+        E = hv[0];
+        rms = hv[1];
+        if (!std::isfinite(E) || !std::isfinite(rms)) {
+            cleanup();
+            set_error("cq_scf_ghf: non-finite energy or error norm");
+            return CQ_ERR_NUMERIC;
+        }
+        const double dE = std::fabs(E - Eold);
+        Eold = E;
+        if (it > 1 && dE < o.e_tol && rms < o.d_tol && final_fp64) {
+            converged = true;
+            break;
+        }
+        if (!final_fp64 && rms < o.switch_tol) final_fp64 = true;
+        const int slot = head;
+        head = (head + 1) % o.diis_size;
+        nvec = nvec < o.diis_size ? nvec + 1 : nvec;
+        CQ_CUDA(cudaMemcpyAsync(Fs[slot], F2, NN * sizeof(Z), cudaMemcpyDeviceToDevice, s));
+        CQ_CUDA(cudaMemcpyAsync(Es[slot], Ep, MM * sizeof(Z), cudaMemcpyDeviceToDevice, s));
+        int order[DIIS_MAX];
+        for (int k = 0; k < nvec; ++k) order[k] = (head - nvec + k + o.diis_size) % o.diis_size;
+        for (int k = 0; k < nvec; ++k) {
+            dot_kernel<<<1, 256, 0, s>>>(2 * MM, (const double*)Es[slot], (const double*)Es[order[k]], 0.0, 1.0, 0,
+                                         Bm + slot * DIIS_MAX + order[k]);
+            dot_kernel<<<1, 256, 0, s>>>(2 * MM, (const double*)Es[order[k]], (const double*)Es[slot], 0.0, 1.0, 0,
+                                         Bm + order[k] * DIIS_MAX + slot);
+        }
+        const Z* Fuse = F2;
+        if (nvec >= 2) {
+            CQ_CUDA(cudaMemcpyAsync(slots, order, nvec * sizeof(int), cudaMemcpyHostToDevice, s));
+            diis_solve_kernel<<<1, 32, 0, s>>>(nvec, Bm, slots, coef);
+            FPtrs fp;
+            for (int k = 0; k < nvec; ++k) fp.p[k] = (const double*)Fs[order[k]];
+            // real coefficients: combine the interleaved (re, im) arrays
+            diis_combine_kernel<<<nblk(2 * NN), 256, 0, s>>>(2 * NN, nvec, fp, coef, (double*)Fd);
+            Fuse = Fd;
+        }
+        if ((rc = density_from(Fuse))) { cleanup(); return rc; }
+        CQ_CUDA(cudaGetLastError());
+    }
+    cudaEventRecord(e1, s);
+    CQ_CUDA(cudaMemcpyAsync(P_out, P, 4 * nn * sizeof(Z), cudaMemcpyDeviceToDevice, s));
+    if (F_out) CQ_CUDA(cudaMemcpyAsync(F_out, F, 4 * nn * sizeof(Z), cudaMemcpyDeviceToDevice, s));
+    CQ_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cleanup();
+    st.energy = E;
+    st.iterations = converged ? it : o.max_iter;
+    st.converged = converged ? 1 : 0;
+    st.last_rms = rms;
+    st.ms = ms;
+    if (stats) *stats = st;
+    if (!converged) {
+        set_error("cq_scf_ghf: not converged within max_iter");
+        return CQ_ERR_NOT_CONVERGED;
+    }
     return CQ_OK;
 }

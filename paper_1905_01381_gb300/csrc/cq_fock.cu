@@ -172,7 +172,9 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
     const long long base = c.cls_qoff[qc], top = c.cls_qoff[qc + 1];
     unsigned int n0 = 0, n1 = 0;
     unsigned int o0 = write ? toff[2 * w] : 0, o1 = write ? toff[2 * w + 1] : 0;
-    for (int j0 = t.y; j0 < t.z; j0 += 32) {
+    // a skipped molecule's task has no survivors (the whole warp agrees)
+    const int jend = (mode & 2) ? t.y : t.z;
+    for (int j0 = t.y; j0 < jend; j0 += 32) {
         const int j = j0 + lane;
         const int prec = classify_one(c, Dm, j, t.z, ba, bb, Qb, dab, mode);
         const unsigned m0 = __ballot_sync(0xffffffffu, prec == 0);

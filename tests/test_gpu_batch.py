@@ -147,3 +147,19 @@ def test_converged_molecules_are_skipped(cq):
     # iteration launched before the host saw the last convergence) screen
     # all of its quartets away; equal up to a differing last iteration
     assert abs(int(st["quartets_fp64"]) - tot) <= 0.2 * tot / min(it)
+
+
+def test_guess_fallback_restarts_from_core_guess(cq):
+    """A supplied guess that has not converged after k iterations is
+    replaced by the core guess with a fresh DIIS subspace: from then on each
+    molecule repeats its core-guess trajectory, k iterations later."""
+    items = _uneven(6, 33)
+    nocc = [mol.n_electrons() // 2 for mol, _ in items]
+    b = cq.Basis.batch(items)
+    _, Ec, itc, stc = b.scf_batch(nocc, raise_on_fail=False)
+    bad = b.pack([synth.density(n, 2, 70 + m) for m, n in enumerate(b.mol_n)])
+    _, Ef, itf, stf = b.scf_batch(nocc, D0=bad, guess_fallback=3, raise_on_fail=False)
+    ok = itc < 128
+    assert ok.sum() >= 5
+    assert np.abs(itf[ok].astype(int) - (itc[ok].astype(int) + 3)).max() <= 1
+    assert np.abs(Ef - Ec)[ok].max() < 1e-10

@@ -112,3 +112,27 @@ def test_rt_zero_field_stationary(cq):
     for k in range(6):
         b.rt_step(k, Pp, Pc, dt=0.05)
     assert (Pc - P0).abs().max().item() < 1e-8
+
+
+def test_ghf_scf_matches_oracle(cq, dr):
+    """Two-component SCF: a cation (9 electrons) from a random spinor guess
+    reaches the oracle's GHF energy; the neutral molecule from the
+    (collinear) core guess reaches the RHF energy."""
+    import torch
+    mol, bas = synth.workload_triatomic()
+    sysm = dr.System(mol, bas)
+    b = cq.Basis(mol, bas)
+    P2 = synth.spinor_density(sysm.n, 9, 21)
+    ref = dr.ghf(sysm, 9, P0=P2)
+    assert ref.converged
+    P0 = torch.as_tensor(np.ascontiguousarray(dr.pauli_split(P2)), device="cuda")
+    P, F, st = b.scf_ghf(9, P0=P0)
+    assert st["converged"]
+    assert abs(st["energy"] - ref.energy) < 1e-10, (st["energy"], ref.energy)
+    # the energy of the returned density by the oracle's GHF Fock
+    Pc = P.cpu().numpy()
+    _, E = dr.ghf_fock(sysm, Pc)
+    assert abs(E - st["energy"]) < 1e-10
+    Pn, _, stn = b.scf_ghf(10)
+    assert abs(stn["energy"] - dr.rhf(sysm, 5).energy) < 1e-10
+    assert np.abs(Pn[1:].cpu().numpy()).max() < 1e-10      # collinear, unpolarised
