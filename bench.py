@@ -328,7 +328,9 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e = ws * nrep / (e0.elapsed_time(e1) * 1e-3)
 
-    launches_per_build = 4 + sum(1 for v in cls.values())
+    # density preparation, block maxima, classify (count), scan, classify
+    # (write), counter totals, finalisation + one launch per class and precision
+    launches_per_build = 7 + sum(1 for v in cls.values())
     out = None
     if rk == 0:
         out = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws,

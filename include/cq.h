@@ -183,6 +183,20 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
  * generated recurrence tables through shared memory).  Both give the same
  * J/K to rounding; the choice only changes speed (set by the autotuner). */
 int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
+
+/* Memory bound of the quartet lists (no paper counterpart).  A basis
+ * created while the capacity is C keeps one list of min(C, candidates)
+ * 8-byte entries, where candidates = the shell quartets of every class that
+ * pass no screening yet (about npair^2 / 2).  When the candidates exceed C
+ * (large bases), the basis uses one task per (class, bra pair) and every
+ * build screens, lists and evaluates the quartets of each class in passes of
+ * whole tasks that fit the list, one after the other on the caller's
+ * stream; the cooperative kernel then reads its quartets from the list.
+ * Results are the same up to the order of the FP64 sums.  Default
+ * 3e9 entries (24 GB); CQ_ERR_INVALID_ARG below 1024.  Process-wide;
+ * affects bases created afterwards. */
+int cq_set_list_capacity(long long entries);
+long long cq_get_list_capacity(void);
 int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
 
 /* Autotuner: times both kernel variants of every class with total angular

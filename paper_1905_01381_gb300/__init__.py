@@ -112,6 +112,8 @@ def lib():
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
         L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.cq_set_list_capacity.argtypes = [ctypes.c_longlong]
+        L.cq_get_list_capacity.restype = ctypes.c_longlong
         _lib = L
     return _lib
 
@@ -134,6 +136,16 @@ def _ptr(t):
 
 PAIR_CLASSES = ["ss", "ps", "pp", "ds", "dp", "dd"]
 QUARTET_CLASSES = [(X, Y) for X in range(6) for Y in range(X + 1)]
+
+
+def set_list_capacity(entries: int):
+    """Largest quartet list (entries) a basis created afterwards keeps; larger
+    bases build in passes (see cq_set_list_capacity)."""
+    check(lib().cq_set_list_capacity(int(entries)), "cq_set_list_capacity")
+
+
+def get_list_capacity() -> int:
+    return int(lib().cq_get_list_capacity())
 
 
 def peak_fma(fp32: bool, iters: int = 20000, stream=None) -> float:

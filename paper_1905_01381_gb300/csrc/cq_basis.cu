@@ -1,6 +1,7 @@
 // Basis set-up: shell normalisation, primitive-pair preparation, the Boys
 // table and the Schwarz factors (direct-SCF integral screening).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -150,7 +151,7 @@ static void free_basis(cq_basis* b)
 {
     if (!b) return;
     dense_free(b);
-    void* ptrs[] = {b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
+    void* ptrs[] = {b->d_pass_qoff, b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
                     b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
                     b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,
                     b->d_Kp, b->d_Dmax, b->d_cnt, b->d_coop_tasks, b->d_qlist, b->d_qcount,
@@ -292,6 +293,18 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
     // offers enough warps to fill the GPU (about 32 per SM).
     b->task_off.assign(NQC + 1, 0);
     b->qoff.assign(NQC + 1, 0);
+    {   // candidate quartets over all classes decide the mode
+        long long total = 0;
+        for (int X = 0; X < NPC; ++X)
+            for (int Y = 0; Y <= X; ++Y)
+                for (int m = 0; m < nmol; ++m) {
+                    const long long nbra = b->mol_range(X, m).second - b->mol_range(X, m).first;
+                    const long long nket = b->mol_range(Y, m).second - b->mol_range(Y, m).first;
+                    total += (X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket;
+                }
+        b->passes = total > g_list_capacity;
+        b->list_cap = b->passes ? g_list_capacity : total;
+    }
     std::vector<int4> tasks;
     for (int X = 0, qc = 0; X < NPC; ++X)
         for (int Y = 0; Y <= X; ++Y, ++qc) {
@@ -305,13 +318,14 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
             b->qoff[qc + 1] = b->qoff[qc] + cand;
             int range = (int)std::min<long long>(JK_RANGE, std::max<long long>(4, cand / (152 * 32)));
             range = std::max(4, range & ~3);
+            if (b->passes) range = INT_MAX;   // one task per bra pair
             std::vector<std::pair<double, int4>> tv;
             for (int m = 0; m < nmol; ++m) {
                 const auto br = b->mol_range(X, m), kr = b->mol_range(Y, m);
                 for (int i = br.first; i < br.second; ++i) {
                     const int jb = kr.first, je = (X == Y) ? i + 1 : kr.second;
-                    for (int j0 = jb; j0 < je; j0 += range) {
-                        const int j1 = std::min(je, j0 + range);
+                    for (int j0 = jb; j0 < je; j0 = (je - j0 > range) ? j0 + range : je) {
+                        const int j1 = (je - j0 > range) ? j0 + range : je;
                         double cost = 0.0;
                         for (int j = j0; j < j1; ++j) cost += b->pairs[j].nprim;
                         tv.push_back({cost * b->pairs[i].nprim, make_int4(i, j0, j1, 0)});
@@ -325,6 +339,10 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
             for (auto& t : tv) tasks.push_back(t.second);
         }
     b->task_off[NQC] = (int)tasks.size();
+    if (b->passes) {
+        b->task_cand.assign(tasks.size() + 1, 0);
+        for (size_t t = 0; t < tasks.size(); ++t) b->task_cand[t + 1] = b->task_cand[t] + (tasks[t].z - tasks[t].y);
+    }
 
     // ---- device copies
     int rc;
@@ -339,7 +357,11 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
     if ((rc = upload(&b->d_tasks, tasks))) return rc;
     if ((rc = upload(&b->d_task_off, b->task_off))) return rc;
     if ((rc = upload(&b->d_qoff, b->qoff))) return rc;
-    if ((rc = dalloc(&b->d_qlist, (size_t)b->qoff[NQC]))) return rc;
+    if ((rc = dalloc(&b->d_qlist, (size_t)b->list_cap))) return rc;
+    if (b->passes) {
+        std::vector<long long> pq = {0, b->list_cap};
+        if ((rc = upload(&b->d_pass_qoff, pq))) return rc;
+    }
     if ((rc = dalloc(&b->d_qcount, 2 * NQC))) return rc;
     if ((rc = dalloc(&b->d_tcount, 2 * tasks.size()))) return rc;
     if ((rc = dalloc(&b->d_toff, 2 * tasks.size()))) return rc;
@@ -399,6 +421,10 @@ int ensure_coop_tasks(cq_basis* b)
     if (!b->coop_dirty) return CQ_OK;
     std::vector<int4> tasks;
     b->coop_off.assign(NQC + 1, 0);
+    if (b->passes) {   // the cooperative kernel reads the passes' lists instead
+        b->coop_dirty = false;
+        return CQ_OK;
+    }
     for (int X = 0, qc = 0; X < NPC; ++X)
         for (int Y = 0; Y <= X; ++Y, ++qc) {
             b->coop_off[qc] = (int)tasks.size();

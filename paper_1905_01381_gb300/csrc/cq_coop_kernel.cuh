@@ -56,12 +56,21 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
     if (w >= a.ntasks) return;
     // task: bra pair, ket pair, primitive-quartet range [p0, p1).  HRR and
     // digestion are linear, so a chunk of primitive quartets is digested on
-    // its own and the J'/K' adds of all chunks sum to the quartet's.
-    const int4 t = a.tasks[w];
-    const int ib = t.x, j = t.y, p0 = t.z, p1 = t.w;
+    // its own and the J'/K' adds of all chunks sum to the quartet's.  In
+    // list mode the task is a screened quartet of the list, all primitives.
+    int4 t;
+    if (a.coop_list) {
+        if (w >= (int)*a.qcount) return;
+        const int2 e = a.qlist[(long long)w * a.qdir];
+        t = make_int4(e.x, e.y, 0, 0);
+    } else {
+        t = a.tasks[w];
+    }
+    const int ib = t.x, j = t.y, p0 = t.z;
     const PairHdr B = a.pairs[ib];
     const PairHdr K = a.pairs[j];
-    {
+    const int p1 = a.coop_list ? B.nprim * K.nprim : t.w;
+    if (!a.coop_list) {
         const float* Dm = a.Dmax;
         const int ns = a.nsh;
         const float* Ds = Dm + B.smbase;

@@ -17,6 +17,8 @@
 // to P^0..P^3 (eight real K matrices, J from Re P^0).
 #include <cstring>
 
+#include <algorithm>
+
 #include "cq_internal.h"
 #include "cq_jk.cuh"
 
@@ -193,14 +195,12 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
     }
 }
 
-// Pass 2: per class (one CTA each), exclusive scan of the task counts into
-// offsets within the class's region, and the list lengths.
-__global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const unsigned int* __restrict__ tcount,
-                                  unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
+// Exclusive scan (one CTA) of the per-task survivor counts of tasks
+// [t0, t1) into offsets within their list region, and the list lengths.
+__device__ __forceinline__ void scan_range(int t0, int t1, const unsigned int* __restrict__ tcount,
+                                          unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
 {
     __shared__ unsigned int part[2][1024];
-    const int qc = blockIdx.x;
-    const int t0 = cls_task_off[qc], t1 = cls_task_off[qc + 1];
     const int n = t1 - t0;
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int b0 = t0 + threadIdx.x * per, b1 = min(t1, b0 + per);
@@ -216,8 +216,8 @@ __global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const un
             part[0][i] = a0; part[1][i] = a1;
             a0 += x0; a1 += x1;
         }
-        qcount[2 * qc] = a0;
-        qcount[2 * qc + 1] = a1;
+        qcount[0] = a0;
+        qcount[1] = a1;
     }
     __syncthreads();
     unsigned int a0 = part[0][threadIdx.x], a1 = part[1][threadIdx.x];
@@ -225,6 +225,89 @@ __global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const un
         toff[2 * t] = a0; toff[2 * t + 1] = a1;
         a0 += tcount[2 * t]; a1 += tcount[2 * t + 1];
     }
+}
+
+// Pass 2: per class (one CTA each), the scan over the class's tasks.
+__global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const unsigned int* __restrict__ tcount,
+                                  unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
+{
+    const int qc = blockIdx.x;
+    scan_range(cls_task_off[qc], cls_task_off[qc + 1], tcount, toff, qcount + 2 * qc);
+}
+
+// The same over the n tasks of one pass (one CTA).
+__global__ void scan_pass_kernel(int n, const unsigned int* __restrict__ tcount, unsigned int* __restrict__ toff,
+                                 unsigned int* __restrict__ qcount)
+{
+    scan_range(0, n, tcount, toff, qcount);
+}
+
+static const int CLASS_ORDER[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
+
+// Large bases: per class, runs of whole tasks whose candidates fit the list
+// are screened into it and drained by the class kernel(s) in turn, on one
+// stream.  The cooperative kernel reads its quartets from the list.
+static int launch_passes(const cq_basis* b, JKArgs& a, ClassifyArgs c, const cq_fock_opts& o, bool profile,
+                         cudaStream_t s)
+{
+    cq_basis* bm = const_cast<cq_basis*>(b);
+    const long long cap = std::min<long long>(b->list_cap, 1LL << 30);
+    c.cls_qoff = b->d_pass_qoff;   // FP64 entries from the front, FP32 from the back of the list
+    const int npp = o.prec == CQ_PREC_FP64 ? 1 : 2;
+    for (int oi = 0; oi < NQC; ++oi) {
+        const int qc = CLASS_ORDER[oi];
+        const int t0 = b->task_off[qc], t1 = b->task_off[qc + 1];
+        if (t0 == t1) continue;
+        int X = 0;
+        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+        const int Y = qc - X * (X + 1) / 2;
+        a.ket_end = b->cls_off[Y + 1];
+        a.same_class = (X == Y);
+        if (profile)
+            for (int pp = 0; pp < npp; ++pp) {
+                for (int e = 0; e < 2; ++e)
+                    if (!bm->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&bm->pev[qc][pp][e]));
+                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][0], s));
+            }
+        for (int ta = t0; ta < t1;) {
+            const long long base = b->task_cand[ta];
+            int tb = (int)(std::upper_bound(b->task_cand.begin() + ta + 1, b->task_cand.begin() + t1 + 1, base + cap) -
+                           b->task_cand.begin()) - 1;
+            if (tb <= ta) {
+                set_error("cq_fock_build: one bra pair has more candidate quartets than the list capacity");
+                return CQ_ERR_UNSUPPORTED;
+            }
+            const long long cand = b->task_cand[tb] - base;
+            c.tasks = b->d_tasks + ta;
+            c.ntasks = tb - ta;
+            const int blocks = (int)(((long long)c.ntasks * 32 + 255) / 256);
+            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 0, b->d_tcount + 2 * (size_t)ta, nullptr);
+            scan_pass_kernel<<<1, 1024, 0, s>>>(c.ntasks, b->d_tcount + 2 * (size_t)ta, b->d_toff + 2 * (size_t)ta,
+                                                b->d_qcount + 2 * qc);
+            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 1, nullptr, b->d_toff + 2 * (size_t)ta);
+            a.tasks = c.tasks;
+            a.ntasks = c.ntasks;
+            a.qmax = cand;
+            for (int pp = 0; pp < npp; ++pp) {
+                a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
+                a.qlist = pp == 0 ? b->d_qlist : b->d_qlist + (b->list_cap - 1);
+                a.qdir = pp == 0 ? 1 : -1;
+                a.qcount = b->d_qcount + 2 * qc + pp;
+                unsigned long long* base_cnt = a.counters;
+                a.counters = base_cnt + 4 * qc + 2 * pp;
+                launch_jk_class(b, a, qc, pp, s);
+                a.counters = base_cnt;
+            }
+            CQ_CUDA(cudaGetLastError());
+            ta = tb;
+        }
+        if (profile)
+            for (int pp = 0; pp < npp; ++pp) {
+                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][1], s));
+                bm->pev_used[qc][pp] = true;
+            }
+    }
+    return CQ_OK;
 }
 
 // Screen and split every candidate quartet into the per-class lists (one
@@ -240,6 +323,7 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->lds;
     c.tau = a.tau; c.tau_mixed = a.tau_mixed; c.split = o.prec == CQ_PREC_MIXED;
     c.qlist = b->d_qlist; c.qcount = b->d_qcount;
+    if (b->passes) return launch_passes(b, a, c, o, profile, s);
     if (c.ntasks > 0) {
         const int blocks = (c.ntasks * 32 + 255) / 256;
         classify_kernel<<<blocks, 256, 0, s>>>(c, NQC, 0, b->d_tcount, nullptr);
@@ -247,7 +331,7 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
         classify_kernel<<<blocks, 256, 0, s>>>(c, NQC, 1, nullptr, b->d_toff);
     }
     CQ_CUDA(cudaGetLastError());
-    static const int order[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
+    const int* order = CLASS_ORDER;
     cq_basis* bm = const_cast<cq_basis*>(b);
     // fork: the class kernels are independent (they only add into J'/K'), so
     // they run on side streams that wait for the classification; the main
@@ -303,7 +387,12 @@ void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaS
 {
     // a class switched to the cooperative kernel uses it once its task list
     // has been rebuilt (by the next cq_fock_build); until then, lane groups
-    if (b->variant[qc][fp32] == VARIANT_COOP && !b->coop_dirty) {
+    if (b->variant[qc][fp32] == VARIANT_COOP && b->passes) {
+        JKArgs c = a;
+        c.coop_list = 1;
+        c.ntasks = (int)a.qmax;
+        if (c.ntasks > 0) launch_coop(c, qc, fp32, s);
+    } else if (b->variant[qc][fp32] == VARIANT_COOP && !b->coop_dirty) {
         JKArgs c = a;
         c.tasks = b->d_coop_tasks + b->coop_off[qc];
         c.ntasks = b->coop_off[qc + 1] - b->coop_off[qc];
@@ -316,6 +405,22 @@ void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaS
 }  // namespace cq
 
 using namespace cq;
+
+namespace cq {
+long long g_list_capacity = 3000000000LL;
+}
+
+extern "C" int cq_set_list_capacity(long long entries)
+{
+    if (entries < 1024) {
+        set_error("cq_set_list_capacity: capacity below 1024 entries");
+        return CQ_ERR_INVALID_ARG;
+    }
+    g_list_capacity = entries;
+    return CQ_OK;
+}
+
+extern "C" long long cq_get_list_capacity(void) { return g_list_capacity; }
 
 extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
 {

@@ -147,12 +147,21 @@ struct cq_basis {
     cudaEvent_t join_ev[NSIDE] = {};
     int4* d_coop_tasks = nullptr;
     bool coop_dirty = true;
+    // large bases: one task per (class, bra pair) and a quartet list of
+    // list_cap entries filled and drained in passes of whole tasks
+    bool passes = false;
+    long long list_cap = 0;
+    std::vector<long long> task_cand;   // prefix sums of candidates over tasks (passes only)
+    long long* d_pass_qoff = nullptr;   // {0, list_cap}
     // private stream of the batched SCF (graph capture needs a non-default stream)
     cudaStream_t batch_stream = nullptr;
     cudaEvent_t batch_ev = nullptr;
 };
 
 namespace cq {
+// largest quartet list a basis allocates before switching to passes
+// (settable through cq_set_list_capacity)
+extern long long g_list_capacity;
 constexpr int COOP_CHUNK = 64;   // primitive quartets per cooperative task
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s);
 int ensure_coop_tasks(cq_basis* b);

@@ -39,6 +39,7 @@ struct JKArgs {
     long long qmax;               // capacity of the list (candidate quartets of the class)
     const int* mol_mode;          // optional per-molecule mode (see ClassifyArgs), read by the
     long long lds2;               // cooperative kernel, which screens its own tasks
+    int coop_list;                // cooperative kernel: 1 = quartets from qlist (already screened)
 };
 
 template <typename R>

@@ -163,3 +163,23 @@ def test_guess_fallback_restarts_from_core_guess(cq):
     assert ok.sum() >= 5
     assert np.abs(itf[ok].astype(int) - (itc[ok].astype(int) + 3)).max() <= 1
     assert np.abs(Ef - Ec)[ok].max() < 1e-10
+
+
+def test_batched_scf_in_passes(cq):
+    """The batched SCF on a basis that builds in passes (small list
+    capacity) converges to the same energies, with its graph replay."""
+    items = _uneven(5, 34)
+    nocc = [mol.n_electrons() // 2 for mol, _ in items]
+    ref = cq.Basis.batch(items)
+    _, E0, it0, _ = ref.scf_batch(nocc, raise_on_fail=False)
+    old = cq.get_list_capacity()
+    cq.set_list_capacity(4096)
+    try:
+        b = cq.Basis.batch(items)
+    finally:
+        cq.set_list_capacity(old)
+    _, E1, it1, st1 = b.scf_batch(nocc, raise_on_fail=False)
+    ok = it0 < 128
+    assert ok.sum() >= 4
+    assert np.abs(E1 - E0)[ok].max() < 1e-10
+    assert st1["graph"] >= 1

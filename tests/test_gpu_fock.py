@@ -180,3 +180,33 @@ def test_autotune_keeps_parity(cq, orc):
     Jo, Ko = orc.jk(orc.OBasis(mol, bas), P)
     assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
     assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_bounded_list_passes(cq, orc, variant):
+    """A basis whose candidate quartets exceed the list capacity builds in
+    passes (one task per bra pair, the cooperative kernel reading the list):
+    same J/K as the oracle, FP64 and mixed, every class in each variant."""
+    mol, bas = CASES["OCNH3"]()
+    old = cq.get_list_capacity()
+    cq.set_list_capacity(3000)
+    try:
+        b = cq.Basis(mol, bas)
+    finally:
+        cq.set_list_capacity(old)
+    for qc in range(21):
+        for p in (0, 1):
+            b.set_variant(qc, p, variant)
+    ob = orc.OBasis(mol, bas)
+    P = synth.density(b.nbf, 9, 17, complex_=True)
+    J, K, st = b.fock_build(_gpu(P), stats=True)
+    Jo, Ko = orc.jk(ob, P)
+    assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
+    assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+    ref = cq.Basis(mol, bas)
+    _, _, st_ref = ref.fock_build(_gpu(P), stats=True)
+    assert st["quartets_fp64"] == st_ref["quartets_fp64"]
+    Jm, Km, stm = b.fock_build(_gpu(P), prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, stats=True)
+    assert stm["quartets_fp32"] > 0
+    assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
+    assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
