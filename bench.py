@@ -177,7 +177,7 @@ def cpu_baseline(seconds: float):
 
 # ---------------------------------------------------------------- GPU arm
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic_jk_rt16.json")
-KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh")
+KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "gen_eri.py", "gen_coop.py")
 
 
 def kernel_sources_sha1():
@@ -197,10 +197,12 @@ def traffic_of(key, cls, variant):
         tj = json.load(open(TRAFFIC))
     except (OSError, ValueError):
         return None
-    e = tj.get("launches", {}).get(key)
-    if not e or e.get("variant") != variant or tj.get("sources_sha1") != kernel_sources_sha1():
+    if tj.get("sources_sha1") != kernel_sources_sha1():
         return None
-    return e["bytes_per_quartet"] * cls["quartets"]
+    for e in tj.get("launches", {}).get(key, []):
+        if e.get("variant") == variant:
+            return e["bytes_per_quartet"] * cls["quartets"]
+    return None
 
 
 def run_gpu(args):
@@ -228,10 +230,12 @@ def run_gpu(args):
     flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     # ---- kernel variant per class (autotuner; set-up, not timed)
-    if args.no_autotune:
-        tuned = {"variant": [[b.get_variant(q, 0), b.get_variant(q, 1)] for q in range(21)]}
-    else:
-        tuned = b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=False)
+    if not args.no_autotune:
+        b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=False)
+    for spec in args.variant:          # QC:FP32:VARIANT, after the autotuner
+        q, p32, v = (int(x) for x in spec.split(":"))
+        b.set_variant(q, p32, v)
+    tuned = {"variant": [[b.get_variant(q, 0), b.get_variant(q, 1)] for q in range(21)]}
 
     # ---- accuracy of the timed mode against the all-FP64 build (same run)
     J64, K64 = b.fock_build(P)
@@ -346,6 +350,12 @@ def run_gpu(args):
                "fp64_builds_per_s": fp64_rate if fp64_rate is not None else value,
                "accuracy_vs_fp64_gpu": {"dE_Eh": dE, "max_dJ": dJ, "max_dK": dK},
                "gflops_per_build": {"fp64": tot_flops64 * 1e-9, "fp32": tot_flops32 * 1e-9},
+               # whole build against the time its FLOPs need at the measured
+               # FP64 and FP32 peaks (class kernels run concurrently)
+               "build_roofline": {"min_ms": (tot_flops64 / peak64 + tot_flops32 / peak32) * 1e3,
+                                  "ms": tot_ms / args.steps,
+                                  "frac": (tot_flops64 / peak64 + tot_flops32 / peak32) * 1e3
+                                          / (tot_ms / args.steps)},
                "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved * 1e-12,
                             "peak": dom_peak * 1e-12, "unit": "TFLOP/s", "frac": achieved / dom_peak,
                             "traffic": traffic,
@@ -565,6 +575,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant per class (profiling runs)")
+    ap.add_argument("--variant", action="append", default=[], metavar="QC:FP32:V",
+                    help="set the kernel variant of one class and precision (after autotuning)")
     ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
                          "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")

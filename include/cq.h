@@ -184,6 +184,8 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
  * J/K to rounding; the choice only changes speed (set by the autotuner). */
 int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
 
+int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
+
 /* Memory bound of the quartet lists (no paper counterpart).  A basis
  * created while the capacity is C keeps one list of min(C, candidates)
  * 8-byte entries, where candidates = the shell quartets of every class that
@@ -197,15 +199,17 @@ int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
  * affects bases created afterwards. */
 int cq_set_list_capacity(long long entries);
 long long cq_get_list_capacity(void);
-int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
 
 /* Autotuner: times both kernel variants of every class with total angular
  * momentum >= 4 (lighter classes keep lane groups) on the given density
  * (device, layout as for cq_fock_build) with the given options (NULL:
  * mixed precision, mixed_tol 1e-3), keeps the fastest variant per class and
- * precision in the basis, and returns the choice in table[2*qc + fp32] and
- * the best kernel time in ms_out[2*qc + fp32] (host arrays of 42, either may
- * be NULL).  Runs four builds; allocates and frees two output buffers. */
+ * precision in the basis, then flips the variant of each of the six
+ * costliest classes in turn and keeps a flip only if the median of three
+ * complete (concurrent) builds gets more than 1 % faster.  Returns the
+ * choice in table[2*qc + fp32] and the best isolated kernel time in
+ * ms_out[2*qc + fp32] (host arrays of 42, either may be NULL).  Runs up to
+ * 25 builds; allocates and frees two output buffers. */
 int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts,
                 int* table, double* ms_out, void* stream);
 

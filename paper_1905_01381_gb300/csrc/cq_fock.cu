@@ -18,6 +18,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <vector>
 
 #include "cq_internal.h"
 #include "cq_jk.cuh"
@@ -615,14 +616,61 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
             }
     }
     b->profile = old_profile;
+    if (rc) {
+        cudaFree(J);
+        cudaFree(K);
+        return rc;
+    }
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < 2; ++p) {
+            if (b->variant[q][p] != choice[q][p]) b->coop_dirty = true;
+            b->variant[q][p] = choice[q][p];
+        }
+    // Refinement on the whole build: the class kernels of a build run
+    // concurrently, so a variant that wins alone can lose beside the others.
+    // For the costliest classes, flip the variant and keep the flip only if
+    // the median time of three complete builds improves by more than 1 %.
+    auto build_ms = [&](double* out) -> int {
+        double t[3];
+        for (int r = 0; r < 3; ++r) {
+            cq_fock_stats st;
+            const int e = cq_fock_build(b, kind, P, J, K, &o, &st, stream);
+            if (e) return e;
+            t[r] = st.ms;
+        }
+        std::sort(t, t + 3);
+        *out = t[1];
+        return CQ_OK;
+    };
+    std::vector<std::pair<double, int>> cand;
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++p)
+            if (Lof(q) >= 4 && best[q][p] < 1e299) cand.push_back({best[q][p], 2 * q + p});
+    std::sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
+        return x.first > y.first;
+    });
+    if (cand.size() > 6) cand.resize(6);
+    double cur = 0.0;
+    rc = build_ms(&cur);
+    for (size_t i = 0; i < cand.size() && rc == CQ_OK; ++i) {
+        const int q = cand[i].second / 2, p = cand[i].second % 2;
+        b->variant[q][p] ^= 1;
+        b->coop_dirty = true;
+        double t = 0.0;
+        if ((rc = build_ms(&t))) break;
+        if (t < 0.99 * cur) {
+            cur = t;
+        } else {
+            b->variant[q][p] ^= 1;
+            b->coop_dirty = true;
+        }
+    }
     cudaFree(J);
     cudaFree(K);
     if (rc) return rc;
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < 2; ++p) {
-            if (b->variant[q][p] != choice[q][p]) b->coop_dirty = true;
-            b->variant[q][p] = choice[q][p];
-            if (table) table[2 * q + p] = choice[q][p];
+            if (table) table[2 * q + p] = b->variant[q][p];
             if (ms_out) ms_out[2 * q + p] = best[q][p] < 1e299 ? best[q][p] : 0.0;
         }
     return ensure_coop_tasks(b);

@@ -130,14 +130,51 @@ def pack(x0, x1, x2, x3, x4, out, cs):
     return (w0, w1, w2, w3)
 
 
+def schedule(P, maxlev):
+    """Phases (lists of nodes evaluated between two warp syncs) that fill
+    whole 32-lane groups where the dependencies allow: every node has a
+    window [earliest, latest] phase (latest from its consumers; targets may
+    wait for the last phase); a phase takes the nodes whose window closes
+    there, then tops up each shape's last group with ready nodes whose
+    window is still open (closing soonest first)."""
+    nodes = [k for k in P.order]
+    consumers = {k: [] for k in nodes}
+    for k in nodes:
+        for d in P.nodes[k]["deps"]:
+            if d in consumers:
+                consumers[d].append(k)
+    latest = {}
+    for k in reversed(nodes):   # P.order lists every node after its deps
+        latest[k] = min((latest[c] - 1 for c in consumers[k]), default=maxlev)
+    done = {k: 0 for k in P.nodes if "base" in P.nodes[k]}
+    remaining = list(nodes)
+    phases = []
+    for ph in range(1, maxlev + 1):
+        ready = [k for k in remaining if all(d in done and done[d] < ph for d in P.nodes[k]["deps"])]
+        chosen = []
+        by_shape = {}
+        for k in ready:
+            by_shape.setdefault(P.nodes[k]["shape"], []).append(k)
+        for sh, ks in by_shape.items():
+            must = [k for k in ks if latest[k] <= ph]
+            opt = sorted((k for k in ks if latest[k] > ph), key=lambda k: (latest[k], P.nodes[k]["level"]))
+            room = (-len(must)) % 32
+            chosen += must + opt[:room]
+        assert all(latest[k] > ph for k in remaining if k not in chosen and k in ready)
+        for k in chosen:
+            done[k] = ph
+        cs = set(chosen)
+        remaining = [k for k in remaining if k not in cs]
+        phases.append(chosen)
+    assert not remaining
+    return phases
+
+
 def vrr_program(la, lb, lc, ld):
     P = VRRPlan(la, lb, lc, ld)
     L = P.L
     maxlev = max((P.nodes[k]["level"] for k in P.order), default=0)
-    levels = [[] for _ in range(maxlev + 1)]
-    for k in P.order:
-        levels[P.nodes[k]["level"]].append(k)
-    levels = levels[1:]   # level 0 are the base values
+    levels = schedule(P, maxlev)
     fixed = {k: P.nodes[k]["base"] for k in P.nodes if "base" in P.nodes[k]}
     targets = set(P.targets)
     slot, nslots = allocate(levels, lambda k: P.nodes[k]["deps"], fixed, targets, L + 1)
