@@ -45,6 +45,18 @@ def workload():
     return mol, bas, P
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value of x over the ranks of the process group (x itself
+    without one): the replicas' timed region ends when the slowest ends."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rk = int(os.environ.get("RANK", "0"))
@@ -266,11 +278,7 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(c) for a, c in ev]
-    tot_ms = sum(step_ms)
-    if ws > 1:
-        t = torch.tensor([tot_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = t.item()
+    tot_ms = max_over_ranks(sum(step_ms), "cuda")
     value = ws * args.steps / (tot_ms * 1e-3)
 
     # ---- per-class profile (one extra build, events around each class kernel)

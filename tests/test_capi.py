@@ -61,3 +61,13 @@ def test_invalid_basis_rejected_on_host(libcq):
     assert rc == -1
     rc = libcq.cq_fock_build(None, 0, None, None, None, None, None, None)
     assert rc == -1
+
+
+def test_list_capacity_setting(libcq):
+    old = libcq.cq_get_list_capacity()
+    assert old >= 1024
+    assert libcq.cq_set_list_capacity(10) == -1          # below the minimum: rejected
+    assert libcq.cq_get_list_capacity() == old
+    assert libcq.cq_set_list_capacity(4096) == 0
+    assert libcq.cq_get_list_capacity() == 4096
+    assert libcq.cq_set_list_capacity(old) == 0
