@@ -74,8 +74,9 @@ def gen_sources():
                 f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
                 "{",
                 f"    const long long warps = (a.qmax + {32 // G} - 1) / {32 // G};",
-                "    const long long blocks = (warps * 32 + JK_THREADS - 1) / JK_THREADS;",
+                "    long long blocks = (warps * 32 + JK_THREADS - 1) / JK_THREADS;",
                 "    if (blocks == 0) return;",
+                "    if (blocks > jk_grid_cap()) blocks = jk_grid_cap();",
                 f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<(unsigned)blocks, JK_THREADS, 0, s>>>(a);",
                 "}"]
             if X == Y and tag == "f64":

@@ -409,6 +409,19 @@ using namespace cq;
 
 namespace cq {
 long long g_list_capacity = 3000000000LL;
+
+int jk_grid_cap()
+{
+    static int cap[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1 << 20;
+    if (!cap[dev]) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        cap[dev] = sms * 16;
+    }
+    return cap[dev];
+}
 }
 
 extern "C" int cq_set_list_capacity(long long entries)

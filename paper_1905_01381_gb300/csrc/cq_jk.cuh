@@ -326,13 +326,17 @@ struct ClassifyArgs {
     unsigned int* qcount;         // [NQC][2]
 };
 
-// Lane-group kernel over a compacted quartet list: a group of G lanes
-// evaluates one contracted quartet, its lanes splitting the primitive
-// quartets; accumulators and digested blocks are summed across the group
-// with shuffles.  Warp w takes list entries [w*S, w*S + S), S = 32/G; warps
-// beyond the device-side count return at once.
+// Largest grid (CTAs) of a lane-group launch on the current device: the
+// kernels stride over their list, so longer lists reuse resident warps
+// instead of launching warps that find nothing to do.
+int jk_grid_cap();
+
+// Lane-group evaluation of list chunk w: a group of G lanes evaluates one
+// contracted quartet, its lanes splitting the primitive quartets;
+// accumulators and digested blocks are summed across the group with
+// shuffles.  The chunk is list entries [w*S, w*S + S), S = 32/G.
 template <int LA, int LB, int LC, int LD, typename R, int G>
-__global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
+__device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, const long long cnt)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB), NC = ncart(LC), ND = ncart(LD);
     constexpr int NKB = NA * NC + NA * ND + NB * NC + NB * ND;
@@ -340,8 +344,6 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
     using C = EriClass<LA, LB, LC, LD>;
     const int lane = threadIdx.x & 31;
     const int grp = lane / G, sub = lane - (lane / G) * G;
-    const long long w = ((long long)blockIdx.x * JK_THREADS + threadIdx.x) >> 5;
-    const long long cnt = (long long)*a.qcount;
     if (w * S >= cnt) return;
     const long long idx = w * S + grp;
     const bool on = idx < cnt;
@@ -487,6 +489,18 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
             atomicAdd(a.counters + 1, np);
         }
     }
+}
+
+// Lane-group kernel over a compacted quartet list: warp w evaluates chunks
+// w, w + W, w + 2W, ... (W warps in the grid) until the device-side count.
+template <int LA, int LB, int LC, int LD, typename R, int G>
+__global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
+{
+    constexpr int S = 32 / G;
+    const long long cnt = (long long)*a.qcount;
+    const long long nw = ((long long)gridDim.x * JK_THREADS) >> 5;
+    for (long long w = ((long long)blockIdx.x * JK_THREADS + threadIdx.x) >> 5; w * S < cnt; w += nw)
+        jk_chunk<LA, LB, LC, LD, R, G>(a, w, cnt);
 }
 
 // Schwarz factors of the pairs [begin, end) of class (LA LB): one thread per
