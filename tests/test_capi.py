@@ -71,3 +71,39 @@ def test_list_capacity_setting(libcq):
     assert libcq.cq_set_list_capacity(4096) == 0
     assert libcq.cq_get_list_capacity() == 4096
     assert libcq.cq_set_list_capacity(old) == 0
+
+
+def test_every_entry_point_rejects_null_arguments(libcq):
+    """Host-side validation: each entry point returns CQ_ERR_INVALID_ARG (-1)
+    with a message, before any device work, when its required pointers are
+    NULL or its sizes are out of range."""
+    c_int, c_ll, c_u64 = ctypes.c_int, ctypes.c_longlong, ctypes.c_ulonglong
+    calls = {
+        "cq_basis_layout": (None, None, None, None),
+        "cq_basis_info": (None, None, None, None),
+        "cq_schwarz": (None, None, None),
+        "cq_fock_profile": (None, c_int(1)),
+        "cq_fock_class_stats": (None, c_int(0), c_int(0), None, None, None),
+        "cq_fock_set_variant": (None, c_int(0), c_int(0), c_int(0)),
+        "cq_fock_get_variant": (None, c_int(0), c_int(0), None),
+        "cq_autotune": (None, c_int(0), None, None, None, None, None),
+        "cq_one_electron": (None, None, None, None, None, None, None),
+        "cq_scf": (None, c_int(1), None, None, None, None, None, None),
+        "cq_scf_ghf": (None, c_int(2), None, None, None, None, None, None),
+        "cq_scf_batch": (None, None, None, None, None, None, None, None, None),
+        "cq_rt_step": (None, None, c_int(0), None, None, None, None),
+        "cq_guess_dataset": (None, None, None, None, None, None, None),
+        "cq_guess_density": (None, None, None, c_int(0), c_int(0), None, None),
+        "cq_dense_info": (None, None, None, None),
+        "cq_nuclear_repulsion": (None, None),
+        "cq_nuclear_repulsion_batch": (None, None),
+        "cq_mlp_init": (None, c_u64(0), None),
+        "cq_mlp_loss_grad": (None, c_int(0), None, None, None, None, None, None),
+        "cq_fock_build_noalloc": (None, c_int(0), None, None, None, None, None),
+        "cq_peak_fma": (c_int(0), c_int(0), None, None),
+    }
+    for name, args in calls.items():
+        f = getattr(libcq, name)
+        rc = f(*args)
+        assert rc == -1, (name, rc)
+        assert libcq.cq_last_error(), name
