@@ -379,3 +379,21 @@ def test_jk_elements_match_full(oracle_lib):
     Jo, Ko = oracle_lib.jk_elements(ob, [D], mu, nu)
     assert np.abs(Jo[0] - J[mu, nu]).max() < 1e-13
     assert np.abs(Ko[0] - K[mu, nu]).max() < 1e-13
+
+
+def test_jk_sample_partitions_the_build(oracle_lib):
+    """The timing sample of the CPU baseline: the bra-pair residue classes
+    p % stride partition the unique shell quartets, so the samples add up to
+    the full J and K and their quartet counts to npair (npair + 1) / 2."""
+    mol, bas = synth.small_cluster(3, 21, max_depth=2)
+    ob = oracle_lib.OBasis(mol, bas)
+    D = synth.density(ob.nbf, 4, 6)
+    J, K = oracle_lib.jk_real(ob, [D])
+    stride = 3
+    Js, Ks, nq = 0.0, 0.0, 0
+    for off in range(stride):
+        j, k, n = oracle_lib.jk_sample(ob, [D], stride, off)
+        Js, Ks, nq = Js + j, Ks + k, nq + n
+    npair = ob.nsh * (ob.nsh + 1) // 2
+    assert nq == npair * (npair + 1) // 2
+    assert np.abs(Js - J).max() < 1e-12 and np.abs(Ks - K).max() < 1e-12
