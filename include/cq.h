@@ -26,6 +26,10 @@
  *     synchronise it.
  *   - No entry point aborts or traps.  Every failure returns a negative
  *     cq_status and sets a thread-local message read by cq_last_error().
+ *   - A basis handle holds the scratch of its builds and drivers: calls on
+ *     one handle must not overlap (one host thread, or calls ordered by the
+ *     caller); different handles are independent.  cq_fock_build_noalloc
+ *     shares one scratch array across all handles of a device.
  */
 #ifndef CQ_H
 #define CQ_H
