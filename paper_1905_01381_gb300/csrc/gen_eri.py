@@ -98,7 +98,7 @@ class ClassGen:
             a1 = self.node(e, f1, m + 1)
             expr = f"QC{AX[i]} * {a0}"
             expr = f"fma(WQ{AX[i]}, {a1}, {expr})"
-            self.flops += 2
+            self.flops += 3
             if f1[i] > 0:
                 f2 = sub(f1, i)
                 b0 = self.node(e, f2, m)
