@@ -208,10 +208,13 @@ class RT:
     """Closed-shell RT-TDHF in the orthonormal basis (oracle)."""
 
     def __init__(self, sysm: System, D0: np.ndarray, dt: float, field: Field,
-                 restart: int = 50, nthreads=None):
+                 restart: int = 50, nthreads=None, two_electron: bool = True):
         self.s = sysm
         self.dt, self.field, self.restart = dt, field, restart
         self.nthreads = nthreads
+        self.two_electron = two_electron
+        # two_electron=False propagates under h + V(t) alone (no J, K): a
+        # test-only switch whose exact solution is a plain unitary rotation
         S, X = sysm.S, sysm.X
         self.Xinv = X.T @ S          # X^dagger S maps AO density to ortho: P' = X^+ S P S X
         self.mu = dipole(sysm.ob)    # moment integrals about the origin
@@ -228,7 +231,10 @@ class RT:
 
     def fock(self, Pp, t):
         P = self._to_ao(Pp)
-        F0, E = rhf_fock(self.s, P, self.nthreads)
+        if self.two_electron:
+            F0, E = rhf_fock(self.s, P, self.nthreads)
+        else:
+            F0, E = self.s.h, None
         V = np.tensordot(self.field.at(t), self.mu, axes=1)
         X = self.s.X
         return X.T @ (F0 + V) @ X, E
