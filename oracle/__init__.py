@@ -92,6 +92,17 @@ def boys(mmax: int, T: float) -> np.ndarray:
     return F
 
 
+def boys_quadrature(m: int, T: float, dps: int = 40) -> str:
+    """F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt (the Boys function's
+    definition, Boys 1950) by mpmath quadrature at `dps` digits, returned as
+    a decimal string with 25 significant digits."""
+    import mpmath
+    with mpmath.workdps(dps):
+        T = mpmath.mpf(T)
+        v = mpmath.quad(lambda t: t ** (2 * m) * mpmath.exp(-T * t * t), [0, mpmath.mpf(1) / 2, 1])
+        return mpmath.nstr(v, 25, min_fixed=-1, max_fixed=-1)
+
+
 def _one(ob: OBasis, kind: int, origin=(0.0, 0.0, 0.0)) -> np.ndarray:
     M = np.zeros((ob.nbf, ob.nbf))
     O = np.ascontiguousarray(origin, dtype=np.float64)
@@ -201,4 +212,22 @@ def jk_sample(ob, Ds, stride: int, offset: int = 0, nthreads: int | None = None)
     f.restype = ctypes.c_long
     nq = f(*ob.args(), len(Ds), _d(D), _d(J), _d(K),
            nthreads if nthreads is not None else nthreads_default(), stride, offset)
+    return J, K, int(nq)
+
+
+def jk_sample_pairs(ob, Ds, pairs, nthreads: int | None = None):
+    """J'/K' partial sums over an explicit set of bra shell pairs (pair index
+    a(a+1)/2 + b, a >= b); returns (J, K, shell quartets visited).  Timing
+    support only."""
+    Ds = [np.ascontiguousarray(D, dtype=np.float64) for D in Ds]
+    D = np.ascontiguousarray(np.stack(Ds))
+    J = np.zeros_like(D)
+    K = np.zeros_like(D)
+    sel = np.zeros(ob.nsh * (ob.nsh + 1) // 2, dtype=np.uint8)
+    sel[np.asarray(pairs, dtype=np.int64)] = 1
+    f = lib().or_jk_pairs
+    f.restype = ctypes.c_long
+    nq = f(*ob.args(), len(Ds), _d(D), _d(J), _d(K),
+           nthreads if nthreads is not None else nthreads_default(),
+           sel.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return J, K, int(nq)

@@ -480,7 +480,8 @@ static inline void apply_tuple(int n, int nd, const double *D, double *J,
  * Visits every permutationally unique function quartet once. */
 static long jk_impl(int nsh, const double *ctr, const int *L, const int *np,
            const int *poff, const double *ex, const double *co, int nd,
-           const double *D, double *J, double *K, int nthreads, int stride, int offset)
+           const double *D, double *J, double *K, int nthreads, int stride, int offset,
+           const unsigned char *sel)
 {
     Basis B;
     basis_init(&B, nsh, ctr, L, np, poff, ex, co);
@@ -492,6 +493,21 @@ static long jk_impl(int nsh, const double *ctr, const int *L, const int *np,
     int *pa = (int *)malloc(sizeof(int) * npair), *pb = (int *)malloc(sizeof(int) * npair);
     for (int a = 0, p = 0; a < nsh; ++a)
         for (int b = 0; b <= a; ++b, ++p) { pa[p] = a; pb[p] = b; }
+    /* work items (bra pair, first ket, end of kets): one per bra pair for a
+     * full build; a sample splits its bra pairs' kets into blocks of 64 so
+     * that a few bra pairs still spread over all threads */
+    const int kblk = (sel || stride > 1) ? 64 : npair;
+    long nitem = 0;
+    for (int p1 = npair - 1; p1 >= 0; --p1)
+        if (sel ? sel[p1] : p1 % stride == offset) nitem += (p1 + kblk) / kblk;
+    int *it1 = (int *)malloc(sizeof(int) * (nitem > 0 ? nitem : 1));
+    int *it2 = (int *)malloc(sizeof(int) * (nitem > 0 ? nitem : 1));
+    nitem = 0;
+    for (int p1 = npair - 1; p1 >= 0; --p1)
+        if (sel ? sel[p1] : p1 % stride == offset) {
+            nq += p1 + 1;
+            for (int q = 0; q <= p1; q += kblk) { it1[nitem] = p1; it2[nitem] = q; ++nitem; }
+        }
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -500,12 +516,12 @@ static long jk_impl(int nsh, const double *ctr, const int *L, const int *np,
         double *Jt = (double *)calloc(nn, sizeof(double));
         double *Kt = (double *)calloc(nn, sizeof(double));
         double *blk = (double *)malloc(sizeof(double) * 1296);
-#pragma omp for schedule(dynamic, 1) reduction(+ : nq)
-        for (int p1 = npair - 1; p1 >= 0; --p1) {
-            if (p1 % stride != offset) continue;
-            nq += p1 + 1;
+#pragma omp for schedule(dynamic, 1)
+        for (long w = 0; w < nitem; ++w) {
+            const int p1 = it1[w], q0 = it2[w];
+            const int q1 = q0 + kblk - 1 < p1 ? q0 + kblk - 1 : p1;
             int a = pa[p1], b = pb[p1];
-            for (int p2 = 0; p2 <= p1; ++p2) {
+            for (int p2 = q0; p2 <= q1; ++p2) {
                 int c = pa[p2], d = pb[p2];
                 eri_block(&B, a, b, c, d, blk);
                 int na = NCART[L[a]], nb = NCART[L[b]], nc = NCART[L[c]], ndd = NCART[L[d]];
@@ -541,7 +557,7 @@ static long jk_impl(int nsh, const double *ctr, const int *L, const int *np,
         }
         free(Jt); free(Kt); free(blk);
     }
-    free(pa); free(pb);
+    free(pa); free(pb); free(it1); free(it2);
     basis_free(&B);
     return nq;
 }
@@ -550,7 +566,7 @@ void or_jk(int nsh, const double *ctr, const int *L, const int *np,
            const int *poff, const double *ex, const double *co, int nd,
            const double *D, double *J, double *K, int nthreads)
 {
-    jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, 1, 0);
+    jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, 1, 0, NULL);
 }
 
 /* The same loop restricted to bra shell pairs p with p % stride == offset
@@ -560,7 +576,16 @@ long or_jk_sample(int nsh, const double *ctr, const int *L, const int *np,
                   const int *poff, const double *ex, const double *co, int nd,
                   const double *D, double *J, double *K, int nthreads, int stride, int offset)
 {
-    return jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, stride, offset);
+    return jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, stride, offset, NULL);
+}
+
+/* The same over an explicit set of bra shell pairs (sel[p] != 0, p the
+ * pair index a(a+1)/2 + b, a >= b); timing support only. */
+long or_jk_pairs(int nsh, const double *ctr, const int *L, const int *np,
+                 const int *poff, const double *ex, const double *co, int nd,
+                 const double *D, double *J, double *K, int nthreads, const unsigned char *sel)
+{
+    return jk_impl(nsh, ctr, L, np, poff, ex, co, nd, D, J, K, nthreads, 1, 0, sel);
 }
 
 /* Selected elements straight from the definition, for sampling large cases:
