@@ -103,6 +103,17 @@ int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npair);
 
 void cq_basis_destroy(cq_basis* b);
 
+/* cq_boys: the Boys function F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt,
+ * m = 0..mmax (mmax <= 8), at n arguments, evaluated by the same device
+ * code the integral kernels use (the [00|00]^(m) factor of the Obara-Saika
+ * recurrence, Sec. "Reference Wave Functions" direct integral evaluation):
+ * fp32 = 0 in FP64; fp32 = 1 in FP32 with the argument rounded to FP32 and
+ * FP64 evaluation below T = 1/32 (the first table interval).
+ *   T: device, n doubles.  F: device, n x (mmax + 1) doubles, row-major
+ *   (FP32 results widened).  The table lives in the basis handle b.
+ *   Returns CQ_ERR_INVALID_ARG for mmax outside 0..8, n < 0 or NULL arrays. */
+int cq_boys(const cq_basis* b, int fp32, int mmax, int n, const double* T, double* F, void* stream);
+
 /* cq_schwarz: Schwarz factors Q_ab = sqrt(max_{m in a, n in b} |(mn|mn)|)
  * (screening of the direct build, Sec. "Reference Wave Functions": LinK-like
  * screening).  Q: device, nshell*nshell doubles (row-major, symmetric), or
@@ -149,15 +160,24 @@ int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
  *     block maxima, counters) lives in one file-scope __device__ array of
  *     16 MiB (16777216 bytes) that every GPU loading the library holds until
  *     the library is unloaded.  cq_fock_noalloc_scratch_bytes(kind, nbf,
- *     nshell) gives the bytes a build needs (about (2 nk + 1) nbf^2 doubles,
- *     nk = 1 / 2 / 8 for REAL_SYM / COMPLEX_HERM / PAULI4); a basis that needs
- *     more is rejected with CQ_ERR_INVALID_ARG before any work is enqueued.
+ *     nshell) gives the bytes a build on a single-molecule basis needs
+ *     (about (3 nk + 2) nbf^2 doubles -- nk scaled densities plus the
+ *     two-word J'/K' accumulators -- with nk = 1 / 2 / 8 for REAL_SYM /
+ *     COMPLEX_HERM / PAULI4, so nbf up to about 647 / 512 / 284).  For a batched basis (cq_basis_create_batch)
+ *     the need is that of nmol slots of the largest molecule, more than the
+ *     query reports for the total nbf and nshell: the call itself checks the
+ *     exact need.  A basis that needs more than the array is rejected with
+ *     CQ_ERR_INVALID_ARG before any work is enqueued.
  *   - Arguments, layouts and results are those of cq_fock_build; there is no
  *     stats output.  The basis must come from cq_basis_create (which does
  *     allocate, once, ahead of time).
  *   - The first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  The first launch of the integral kernels in
+ *     (cudaGetSymbolAddress) with that device current.  Under CUDA's lazy
+ *     module loading (the default) that lookup is also what loads the code
+ *     module holding the array, so the 16 MiB are reserved on the device by
+ *     this first call, not when the library is loaded: make the first call
+ *     at set-up -- before the caller's own allocator takes the rest of the
+ *     device memory, and before any stream capture.  The first launch of the integral kernels in
  *     a process may also make the driver enlarge its per-thread local-memory
  *     reservation, so run one build before entering a region where no device
  *     memory may be reserved.
@@ -184,8 +204,12 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
  * cq_fock_class_stats) and precision: 0 = lane-group kernel (lanes of a warp
  * split one quartet's primitive quartets, generated straight-line
  * recurrences), 1 = warp-cooperative kernel (one warp per quartet walking
- * generated recurrence tables through shared memory).  Both give the same
- * J/K to rounding; the choice only changes speed (set by the autotuner). */
+ * generated recurrence tables through shared memory), 2 = axis-permutation
+ * lane groups (FP32 only, classes of total angular momentum >= 5 with a
+ * d shell: 3 or 6 lanes per quartet each run the vertical recurrence for a
+ * third or a sixth of the targets on axis-permuted inputs; CQ_ERR_UNSUPPORTED
+ * elsewhere).  All give the same J/K to rounding; the choice only changes
+ * speed (set by the autotuner). */
 int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
 
 int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
@@ -204,16 +228,17 @@ int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
 int cq_set_list_capacity(long long entries);
 long long cq_get_list_capacity(void);
 
-/* Autotuner: times both kernel variants of every class with total angular
- * momentum >= 4 (lighter classes keep lane groups) on the given density
+/* Autotuner: times every kernel variant a class has (the cooperative one
+ * for total angular momentum >= 4, the axis-permutation one in FP32 where it
+ * exists; lighter classes keep lane groups) on the given density
  * (device, layout as for cq_fock_build) with the given options (NULL:
  * mixed precision, mixed_tol 1e-3), keeps the fastest variant per class and
- * precision in the basis, then flips the variant of each of the six
- * costliest classes in turn and keeps a flip only if the median of three
+ * precision in the basis, then tries the runner-up variant of each of the
+ * six costliest classes in turn and keeps it only if the median of three
  * complete (concurrent) builds gets more than 1 % faster.  Returns the
  * choice in table[2*qc + fp32] and the best isolated kernel time in
  * ms_out[2*qc + fp32] (host arrays of 42, either may be NULL).  Runs up to
- * 25 builds; allocates and frees two output buffers. */
+ * 27 builds; allocates and frees two output buffers. */
 int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts,
                 int* table, double* ms_out, void* stream);
 

@@ -112,6 +112,7 @@ def lib():
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
         L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.cq_boys.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]
         L.cq_set_list_capacity.argtypes = [ctypes.c_longlong]
         L.cq_get_list_capacity.restype = ctypes.c_longlong
         _lib = L
@@ -271,6 +272,16 @@ class Basis:
         Q = torch.empty((self.nshell, self.nshell), dtype=torch.float64, device="cuda")
         check(lib().cq_schwarz(self.h, _ptr(Q), _stream_ptr(stream)), "cq_schwarz")
         return Q
+
+    def boys(self, T, mmax: int, fp32: bool = False, stream=None):
+        """F_0..F_mmax(T) for a CUDA float64 tensor T, evaluated by the
+        integral kernels' device Boys function (FP64 or FP32)."""
+        import torch
+        T = T.contiguous()
+        F = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
+        check(lib().cq_boys(self.h, int(bool(fp32)), int(mmax), int(T.numel()), _ptr(T), _ptr(F),
+                            _stream_ptr(stream)), "cq_boys")
+        return F
 
     def nuclear_repulsion(self) -> float:
         E = ctypes.c_double()

@@ -31,6 +31,11 @@ LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
          "2120": 2, "2111": 2, "2210": 2, "1111": 2}
 
 
+# lanes per shell pair in the Schwarz kernel, by la + lb: the (ab|ab)
+# quartets of one pair have up to MAX_PRIM^4 primitive quartets
+SCHWARZ_LANES = {0: 4, 1: 8, 2: 8, 3: 16, 4: 32}
+
+
 def qclasses():
     out = []
     for i, X in enumerate(PCS):
@@ -84,7 +89,8 @@ def gen_sources():
                         "{",
                         "    const int n = end - begin;",
                         "    if (n <= 0) return;",
-                        f"    schwarz_kernel<{la}, {lb}><<<(n + 63) / 64, 64, 0, s>>>(a, begin, end, Qf, Qd);",
+                        f"    const int per = JK_THREADS / 32 * {32 // SCHWARZ_LANES[la + lb]};",
+                        f"    schwarz_kernel<{la}, {lb}, {SCHWARZ_LANES[la + lb]}><<<(n + per - 1) / per, JK_THREADS, 0, s>>>(a, begin, end, Qf, Qd);",
                         "}"]
             src.append("}  // namespace cq")
             write(os.path.join(GEN, f"cls_{cls}_{tag}.cu"), src)
@@ -104,6 +110,58 @@ def gen_sources():
              ", ".join(f"launch_schwarz_{X[0]}{X[1]}" for X in PCS) + "};")
     d.append("}  // namespace cq")
     write(os.path.join(GEN, "cq_dispatch.cu"), d)
+    # FP32 axis-permutation kernels of the high classes (gen_sym.py): one
+    # translation unit per class, with the class's split recurrence and the
+    # warp-cooperative HRR tables
+    import gen_sym  # noqa: E402
+    qc_of = {f"{X[0]}{X[1]}{Y[0]}{Y[1]}": qc for qc, (X, Y) in enumerate(qclasses())}
+    sym = {}
+    for (la, lb, lc, ld, G) in gen_sym.classes_for_sym():
+        cls = f"{la}{lb}{lc}{ld}"
+        code, _ = gen_sym.emit_class(la, lb, lc, ld, G)
+        path = os.path.join(GEN, f"sym_{cls}.cuh")
+        if not os.path.exists(path) or open(path).read() != code:
+            with open(path, "w") as fh:
+                fh.write(code)
+        sym[cls] = G
+        write(os.path.join(GEN, f"cls_{cls}_sym.cu"), [
+            f"// generated by build.py: class ({cls}), FP32 axis-permutation kernel",
+            '#include "cq_internal.h"',
+            '#include "cq_coop.cuh"',
+            '#include "coop_tables.cuh"',
+            '#include "cq_sym.cuh"',
+            "namespace cq {",
+            f'#include "sym_{cls}.cuh"',
+            f"void launch_sym_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
+            "{",
+            "    if (!fp32) return;",
+            f"    constexpr int qc = {qc_of[cls]}, G = {G}, NGRP = 32 / G, WARPS = SYM_THREADS / 32;",
+            "    const int nslots = COOP_SIZES[qc].nslots;",
+            "    const size_t bytes = (size_t)WARPS * sym_warp_bytes<float>(nslots);",
+            f"    auto kern = jk_sym_kernel<{la}, {lb}, {lc}, {ld}, float, G>;",
+            "    static int attr_done = 0;",
+            "    if (!attr_done) {",
+            "        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);",
+            "        attr_done = 1;",
+            "    }",
+            "    const long long warps = (a.qmax + NGRP - 1) / NGRP;",
+            "    long long blocks = (warps + WARPS - 1) / WARPS;",
+            "    if (blocks == 0) return;",
+            "    if (blocks > jk_grid_cap()) blocks = jk_grid_cap();",
+            "    kern<<<(unsigned)blocks, SYM_THREADS, bytes, s>>>(a, qc, nslots);",
+            "}",
+            "}  // namespace cq"])
+    # dispatch table of the split kernels (NULL where a class has none)
+    d = ['#include "cq_internal.h"', "namespace cq {"]
+    for cls in sym:
+        d.append(f"void launch_sym_{cls}(const JKArgs&, int, cudaStream_t);")
+    entries = []
+    for (X, Y) in qclasses():
+        c = f"{X[0]}{X[1]}{Y[0]}{Y[1]}"
+        entries.append(f"launch_sym_{c}" if c in sym else "nullptr")
+    d.append("const LaunchJK SYM_LAUNCH[NQC] = {" + ", ".join(entries) + "};")
+    d.append("}  // namespace cq")
+    write(os.path.join(GEN, "cq_dispatch_split.cu"), d)
     sys.path.remove(CSRC)
     return tus, stats
 
@@ -120,8 +178,12 @@ def _deps_mtime():
 def _compile(src, verbose=False):
     obj = os.path.join(OBJ, os.path.basename(src).replace(".cu", ".o"))
     dm = max(_deps_mtime(), os.path.getmtime(src))
-    if os.path.basename(src) == "cq_coop.cu":
+    base = os.path.basename(src)
+    is_sym = base.startswith("cls_") and base.endswith("_sym.cu")
+    if base == "cq_coop.cu" or is_sym:
         dm = max(dm, os.path.getmtime(os.path.join(GEN, "coop_tables.cuh")))
+    if is_sym:
+        dm = max(dm, os.path.getmtime(os.path.join(GEN, "sym_" + os.path.basename(src)[4:8] + ".cuh")))
     if os.path.exists(obj) and os.path.getmtime(obj) >= dm:
         return obj, ""
     cmd = ["nvcc", "-c", src, "-o", obj + ".tmp"] + NVFLAGS
@@ -138,9 +200,14 @@ def build(jobs: int | None = None, verbose: bool = False) -> str:
     tus, _ = gen_sources()
     srcs = [os.path.join(CSRC, s) for s in HAND_SOURCES] + tus
     # heaviest TUs first so the parallel build finishes early
-    srcs.sort(key=lambda s: -os.path.getsize(s) if "cls_" not in s else
-              -os.path.getsize(os.path.join(GEN, "eri_" + os.path.basename(s)[4:8] + ".cuh"))
-              * (2 if s.endswith("_f64.cu") else 1))
+    def weight(s):
+        if not os.path.basename(s).startswith("cls_"):
+            return os.path.getsize(s)
+        if s.endswith("_sym.cu"):
+            return 3 * os.path.getsize(os.path.join(GEN, "sym_" + os.path.basename(s)[4:8] + ".cuh"))
+        return (os.path.getsize(os.path.join(GEN, "eri_" + os.path.basename(s)[4:8] + ".cuh"))
+                * (2 if s.endswith("_f64.cu") else 1))
+    srcs.sort(key=lambda s: -weight(s))
     jobs = jobs or max(1, os.cpu_count() or 1)
     with cf.ThreadPoolExecutor(jobs) as ex:
         res = list(ex.map(lambda s: _compile(s, verbose), srcs))

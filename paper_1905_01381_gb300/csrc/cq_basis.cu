@@ -13,13 +13,13 @@ namespace cq {
 
 const int PC_L[NPC][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
 
-// kernel variant per class before tuning (measured on GB300, 210-function
-// s,p,d cluster): the warp-cooperative kernel for the classes with the
-// largest recurrences, (dp|dp) (dd|pp) (dd|dp) (dd|dd) in FP64 and
-// (dd|dp) (dd|dd) in FP32; lane groups elsewhere
+// kernel variant per class before tuning: in FP64 the warp-cooperative
+// kernel for the classes with the largest recurrences, (dp|dp) (dd|pp)
+// (dd|dp) (dd|dd); in FP32 the axis-permutation lane groups for every class
+// of total angular momentum 6 or more; lane groups elsewhere
 const int DEFAULT_VARIANT[NQC][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
                                      {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
-                                     {1, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {1, 1}, {1, 1}};
+                                     {1, 2}, {0, 0}, {0, 0}, {1, 2}, {0, 2}, {1, 2}, {1, 2}};
 
 static thread_local std::string g_err;
 
@@ -165,6 +165,9 @@ static void free_basis(cq_basis* b)
         for (int p = 0; p < 2; ++p)
             for (int e = 0; e < 2; ++e)
                 if (b->pev[q][p][e]) cudaEventDestroy(b->pev[q][p][e]);
+    for (int q = 0; q < NQC; ++q)
+        for (int p = 0; p < 2; ++p)
+            for (cudaEvent_t ev : b->pev_pass[q][p]) cudaEventDestroy(ev);
     for (int k = 0; k < cq_basis::NSIDE; ++k) {
         if (b->side[k]) cudaStreamDestroy(b->side[k]);
         if (b->join_ev[k]) cudaEventDestroy(b->join_ev[k]);
@@ -306,6 +309,10 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
         b->list_cap = b->passes ? g_list_capacity : total;
     }
     std::vector<int4> tasks;
+    // prefix sums of primitive-pair counts over the pair array: the cost of
+    // a task (bra i, kets [j0, j1)) is nprim_i * (pref[j1] - pref[j0])
+    std::vector<long long> npref(b->pairs.size() + 1, 0);
+    for (size_t j = 0; j < b->pairs.size(); ++j) npref[j + 1] = npref[j] + b->pairs[j].nprim;
     for (int X = 0, qc = 0; X < NPC; ++X)
         for (int Y = 0; Y <= X; ++Y, ++qc) {
             b->task_off[qc] = (int)tasks.size();
@@ -326,8 +333,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
                     const int jb = kr.first, je = (X == Y) ? i + 1 : kr.second;
                     for (int j0 = jb; j0 < je; j0 = (je - j0 > range) ? j0 + range : je) {
                         const int j1 = (je - j0 > range) ? j0 + range : je;
-                        double cost = 0.0;
-                        for (int j = j0; j < j1; ++j) cost += b->pairs[j].nprim;
+                        const double cost = (double)(npref[j1] - npref[j0]);
                         tv.push_back({cost * b->pairs[i].nprim, make_int4(i, j0, j1, 0)});
                     }
                 }
@@ -421,7 +427,24 @@ int ensure_coop_tasks(cq_basis* b)
     if (!b->coop_dirty) return CQ_OK;
     std::vector<int4> tasks;
     b->coop_off.assign(NQC + 1, 0);
-    if (b->passes) {   // the cooperative kernel reads the passes' lists instead
+    // Large bases: the cooperative kernel reads the screened quartet lists
+    // (one warp per quartet, all its primitives) instead of a task per
+    // candidate quartet and primitive chunk, whose table would grow with
+    // the candidate count.
+    long long cand = 0;
+    for (int X = 0, qc = 0; X < NPC; ++X)
+        for (int Y = 0; Y <= X; ++Y, ++qc) {
+            if (b->variant[qc][0] != VARIANT_COOP && b->variant[qc][1] != VARIANT_COOP) continue;
+            for (int m = 0; m < b->nmol; ++m) {
+                const long long nbra = b->mol_range(X, m).second - b->mol_range(X, m).first;
+                const long long nket = b->mol_range(Y, m).second - b->mol_range(Y, m).first;
+                cand += (X == Y) ? nbra * (nbra + 1) / 2 : nbra * nket;
+            }
+        }
+    b->coop_list = b->passes || cand > COOP_TASK_CANDIDATES;
+    if (b->coop_list) {
+        if (b->d_coop_tasks) cudaFree(b->d_coop_tasks);
+        b->d_coop_tasks = nullptr;
         b->coop_dirty = false;
         return CQ_OK;
     }
@@ -556,6 +579,46 @@ extern "C" int cq_basis_info(const cq_basis* b, int* nbf, int* nshell, int* npai
     if (nbf) *nbf = b->nbf;
     if (nshell) *nshell = b->nsh;
     if (npair) *npair = b->npair;
+    return CQ_OK;
+}
+
+// Boys values F_0..F_mmax at n arguments with the same device functions the
+// integral kernels use (FP64, or FP32 with FP64 below the first table
+// interval); results widened to FP64, row-major n x (mmax + 1).
+template <typename R>
+__global__ void boys_eval_kernel(int mmax, int n, const double* __restrict__ T, const double* __restrict__ tabd,
+                                 const float* __restrict__ tabf, double* __restrict__ F)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const R t = (R)T[i];
+    R f[LTOT_MAX + 1];
+    switch (mmax) {
+        case 0: boys_q<0>(t, f, tabd, tabf); break;
+        case 1: boys_q<1>(t, f, tabd, tabf); break;
+        case 2: boys_q<2>(t, f, tabd, tabf); break;
+        case 3: boys_q<3>(t, f, tabd, tabf); break;
+        case 4: boys_q<4>(t, f, tabd, tabf); break;
+        case 5: boys_q<5>(t, f, tabd, tabf); break;
+        case 6: boys_q<6>(t, f, tabd, tabf); break;
+        case 7: boys_q<7>(t, f, tabd, tabf); break;
+        default: boys_q<8>(t, f, tabd, tabf); break;
+    }
+    for (int m = 0; m <= mmax; ++m) F[(size_t)i * (mmax + 1) + m] = (double)f[m];
+}
+
+extern "C" int cq_boys(const cq_basis* b, int fp32, int mmax, int n, const double* T, double* F, void* stream)
+{
+    if (!b || (n > 0 && (!T || !F)) || mmax < 0 || mmax > LTOT_MAX || n < 0 || fp32 < 0 || fp32 > 1) {
+        set_error("cq_boys: bad argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    if (n == 0) return CQ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int blocks = (n + 127) / 128;
+    if (fp32) boys_eval_kernel<float><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
+    else boys_eval_kernel<double><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
+    CQ_CUDA(cudaGetLastError());
     return CQ_OK;
 }
 

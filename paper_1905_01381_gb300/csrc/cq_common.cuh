@@ -122,14 +122,88 @@ __device__ __forceinline__ void boys(float T, float* F, const float* __restrict_
             for (int m = L - 1; m >= 0; --m) F[m] = fmaf(t2, F[m + 1], e) * (1.0f / (2 * m + 1));
         }
     } else {
-        const float rs = rsqrtf(T);
-        F[0] = 0.886226925f * rs;
+        // correctly rounded 1/T and sqrt keep the upward recursion within a
+        // few ulp of F_m over m <= 8
+        const float it = 1.0f / T;
+        F[0] = 0.886226925f * sqrtf(it);
         if (L > 0) {
             const float e = __expf(-T);
-            const float o2t = 0.5f * rs * rs;
+            const float o2t = 0.5f * it;
 #pragma unroll
             for (int m = 0; m < L; ++m) F[m + 1] = fmaf((float)(2 * m + 1), F[m], -e) * o2t;
         }
+    }
+}
+
+// ------------------------------------------------ J'/K' accumulation
+// Order-independent accumulation.  Every contribution v is added to its
+// element as the integer X = trunc(v 2^80), held in two signed 64-bit words:
+// hi = trunc(X / 2^40) (units of 2^-40) and lo = X - hi 2^40 (units of
+// 2^-80, |lo| < 2^40).  Integer addition is associative, so the sums --
+// and the J, K built from them -- are the same bit for bit whatever the
+// order of the adds (concurrent class kernels, warps, atomics).  Range:
+// |element| < 2^22 and fewer than 2^23 adds per element; resolution 2^-80
+// per add.  An element e occupies words 2e (hi) and 2e + 1 (lo).
+using acc_t = unsigned long long;
+constexpr double FX_HI_UNIT = 9.094947017729282379e-13;   // 2^-40
+constexpr double FX_LO_UNIT = 8.271806125530276749e-25;   // 2^-80
+
+__device__ __forceinline__ void fx_add(acc_t* __restrict__ acc, size_t e, double v)
+{
+    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+    const int ex = (int)((u >> 52) & 0x7ff);
+    int sh = ex - 1075 + 80;             // |v| 2^80 = man 2^sh
+    if (ex == 0 || sh <= -53) return;    // zero, subnormal or below 2^-80
+    if (sh > 49) sh = 49;                // |v| >= 2^22: outside the documented range (saturates)
+    const unsigned long long man = (u & 0xfffffffffffffull) | (1ull << 52);
+    const unsigned long long mask40 = (1ull << 40) - 1;
+    unsigned long long mh, ml;
+    if (sh < 0) {
+        const unsigned long long m = man >> (-sh);
+        mh = m >> 40;
+        ml = m & mask40;
+    } else if (sh < 40) {
+        mh = man >> (40 - sh);
+        ml = (man << sh) & mask40;
+    } else {
+        mh = man << (sh - 40);
+        ml = 0;
+    }
+    const bool neg = (u >> 63) != 0;
+    if (mh) atomicAdd(acc + 2 * e, neg ? (unsigned long long)(-(long long)mh) : mh);
+    if (ml) atomicAdd(acc + 2 * e + 1, neg ? (unsigned long long)(-(long long)ml) : ml);
+}
+
+// Value of the integer sum (hi, lo) (signed words), rounded once to FP64.
+__host__ __device__ __forceinline__ double fx_value(long long hi, long long lo)
+{
+    return (double)hi * FX_HI_UNIT + (double)lo * FX_LO_UNIT;
+}
+
+// Boys values of a primitive quartet in its kernel's precision.  FP32
+// quartets keep FP64 near the small-T branch: below the first table interval
+// (T < 1/32) the values come from the FP64 expansion around T = 0 and are
+// rounded to FP32 once.
+constexpr float BOYS_FP64_BELOW = 0.03125f;
+
+template <int L>
+__device__ __forceinline__ void boys_q(double T, double* F, const double* __restrict__ tabd,
+                                       const float* __restrict__)
+{
+    boys<L>(T, F, tabd);
+}
+
+template <int L>
+__device__ __forceinline__ void boys_q(float T, float* F, const double* __restrict__ tabd,
+                                       const float* __restrict__ tabf)
+{
+    if (T < BOYS_FP64_BELOW) {
+        double Fd[L + 1];
+        boys<L>((double)T, Fd, tabd);
+#pragma unroll
+        for (int m = 0; m <= L; ++m) F[m] = (float)Fd[m];
+    } else {
+        boys<L>(T, F, tabf);
     }
 }
 

@@ -6,18 +6,18 @@
 namespace cq {
 
 template <typename R>
-__device__ __forceinline__ void boys_rt_any(int L, R T, R* F, const R* tab)
+__device__ __forceinline__ void boys_rt_any(int L, R T, R* F, const double* td, const float* tf)
 {
     switch (L) {
-        case 0: boys<0>(T, F, tab); break;
-        case 1: boys<1>(T, F, tab); break;
-        case 2: boys<2>(T, F, tab); break;
-        case 3: boys<3>(T, F, tab); break;
-        case 4: boys<4>(T, F, tab); break;
-        case 5: boys<5>(T, F, tab); break;
-        case 6: boys<6>(T, F, tab); break;
-        case 7: boys<7>(T, F, tab); break;
-        default: boys<8>(T, F, tab); break;
+        case 0: boys_q<0>(T, F, td, tf); break;
+        case 1: boys_q<1>(T, F, td, tf); break;
+        case 2: boys_q<2>(T, F, td, tf); break;
+        case 3: boys_q<3>(T, F, td, tf); break;
+        case 4: boys_q<4>(T, F, td, tf); break;
+        case 5: boys_q<5>(T, F, td, tf); break;
+        case 6: boys_q<6>(T, F, td, tf); break;
+        case 7: boys_q<7>(T, F, td, tf); break;
+        default: boys_q<8>(T, F, td, tf); break;
     }
 }
 
@@ -35,6 +35,117 @@ __device__ __forceinline__ int coop_node(int shape, const int4 d, const R* __res
     }
     if (shape >= 2) v = fma(cf[(cw >> 24) & 63], V[d.z & 0xffff], v);
     return (unsigned)d.z >> 16;
+}
+
+// Horizontal recurrence and output-stationary digestion of one contracted
+// quartet whose [e0|f0] block sits in V[C.N + t] (t = ie |F| + jf): the
+// warp walks the HRR table, then every lane owns whole J'/K' elements of the
+// quartet's six blocks.  All 32 lanes take part.
+template <typename R>
+__device__ __forceinline__ void coop_hrr_digest(const CoopClass& C, R* __restrict__ V, R* __restrict__ Db,
+                                                R* __restrict__ hc, const PairHdr& B, const PairHdr& K, int ib,
+                                                int j, const JKArgs& a, int lane)
+{
+    const int NA = ncart(C.la), NB = ncart(C.lb), NC = ncart(C.lc), ND = ncart(C.ld);
+    const int n = a.nbf;
+    if (lane < 3) { hc[lane] = (R)B.AB[lane]; hc[3 + lane] = (R)K.AB[lane]; }
+    __syncwarp();
+    for (int g = 0; g < C.nhg; ++g) {
+        const int4 G = __ldg(C.hgrp + g);
+        if (lane < G.y) {
+            const int4 d = __ldg(C.hdesc + G.z + lane);
+            const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
+            const R v = (G.x == 0) ? fma(hc[d.w & 63], V[x1], V[x0]) : V[x0];
+            V[(unsigned)d.z >> 16] = v;
+        }
+        if (G.w) __syncwarp();
+    }
+    __syncwarp();
+
+    // ---- output-stationary digestion
+    R sdeg = R(1);
+    if (B.a == B.b) sdeg *= R(0.5);
+    if (K.a == K.b) sdeg *= R(0.5);
+    if (j == ib) sdeg *= R(0.5);
+    const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
+    const long long mb = B.mbase;
+    const int nJ = (a.want_j ? NA * NB + NC * ND : 0);
+    const int nK = (a.want_k ? NA * NC + NA * ND + NB * NC + NB * ND : 0);
+    for (int q = 0; q < a.nk; ++q) {
+        if (q > 0 && !a.want_k) break;
+        const double* Dq = a.D + (size_t)q * a.mstride;
+        acc_t* Kq = a.K + 2 * (size_t)q * a.mstride;
+        // density blocks: ab, cd, bd, bc, ad, ac (each <= 36)
+        for (int e = lane; e < 216; e += 32) {
+            const int blk = e / 36, r = e - blk * 36;
+            int rr = 0, cc = 0, nr = 0, ncol = 0;
+            switch (blk) {
+                case 0: nr = NA; ncol = NB; rr = fa; cc = fb; break;
+                case 1: nr = NC; ncol = ND; rr = fc; cc = fd; break;
+                case 2: nr = NB; ncol = ND; rr = fb; cc = fd; break;
+                case 3: nr = NB; ncol = NC; rr = fb; cc = fc; break;
+                case 4: nr = NA; ncol = ND; rr = fa; cc = fd; break;
+                default: nr = NA; ncol = NC; rr = fa; cc = fc; break;
+            }
+            if (r < nr * ncol) Db[e] = ldR<R>(Dq + mb + (size_t)(rr + r / ncol) * n + cc + r % ncol);
+        }
+        __syncwarp();
+        const int nout = (q == 0 ? nJ : 0) + nK;
+        for (int o = lane; o < nout; o += 32) {
+            int kind = 0, oo = o;
+            if (q != 0) kind = 2;
+            if (q == 0 && oo >= nJ) { kind = 2; oo -= nJ; }
+            R sum = R(0);
+            acc_t* dst;
+            size_t de;
+            double f;
+            if (kind == 0 && oo < NA * NB) {            // J'_ab
+                const int m = oo / NB, k = oo % NB;
+                for (int ls = 0; ls < NC * ND; ++ls) sum = fma(V[(m * NB + k) * NC * ND + ls], Db[36 + ls], sum);
+                dst = a.J; de = mb + (size_t)(fa + m) * n + fb + k;
+                f = 2.0 * (double)sdeg;
+            } else if (kind == 0) {                       // J'_cd
+                oo -= NA * NB;
+                const int l = oo / ND, s = oo % ND;
+                for (int mk = 0; mk < NA * NB; ++mk) sum = fma(V[mk * NC * ND + l * ND + s], Db[mk], sum);
+                dst = a.J; de = mb + (size_t)(fc + l) * n + fd + s;
+                f = 2.0 * (double)sdeg;
+            } else if (oo < NA * NC) {                    // K'_ac += (ab|cd) D_bd
+                const int m = oo / NC, l = oo % NC;
+                for (int k = 0; k < NB; ++k)
+                    for (int s = 0; s < ND; ++s)
+                        sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[72 + k * ND + s], sum);
+                dst = Kq; de = mb + (size_t)(fa + m) * n + fc + l;
+                f = (double)sdeg;
+            } else if (oo < NA * NC + NA * ND) {          // K'_ad += (ab|cd) D_bc
+                oo -= NA * NC;
+                const int m = oo / ND, s = oo % ND;
+                for (int k = 0; k < NB; ++k)
+                    for (int l = 0; l < NC; ++l)
+                        sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[108 + k * NC + l], sum);
+                dst = Kq; de = mb + (size_t)(fa + m) * n + fd + s;
+                f = (double)sdeg;
+            } else if (oo < NA * NC + NA * ND + NB * NC) {  // K'_bc += (ab|cd) D_ad
+                oo -= NA * NC + NA * ND;
+                const int k = oo / NC, l = oo % NC;
+                for (int m = 0; m < NA; ++m)
+                    for (int s = 0; s < ND; ++s)
+                        sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[144 + m * ND + s], sum);
+                dst = Kq; de = mb + (size_t)(fb + k) * n + fc + l;
+                f = (double)sdeg;
+            } else {                                       // K'_bd += (ab|cd) D_ac
+                oo -= NA * NC + NA * ND + NB * NC;
+                const int k = oo / ND, s = oo % ND;
+                for (int m = 0; m < NA; ++m)
+                    for (int l = 0; l < NC; ++l)
+                        sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[180 + m * NC + l], sum);
+                dst = Kq; de = mb + (size_t)(fb + k) * n + fd + s;
+                f = (double)sdeg;
+            }
+            fx_add(dst, de, f * (double)sum);
+        }
+        __syncwarp();
+    }
 }
 
 template <typename R>
@@ -87,10 +198,6 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
         else if (a.prec_sel == 2) sel = sel && bound < tm;
         if (!sel) return;
     }
-    const int NA = ncart(C.la), NB = ncart(C.lb), NC = ncart(C.lc), ND = ncart(C.ld);
-    const R* boys_tab;
-    if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
-    const int n = a.nbf;
     unsigned long long nq = 0, np = 0;
     {
         // ---- primitive quartets: coefficients, VRR, accumulation
@@ -113,7 +220,7 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
                 const R roz = kp.zeta * is, roe = bp.zeta * is;
                 const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
                 R F[LTOT_MAX + 1];
-                boys_rt_any<R>(C.L, T, F, boys_tab);
+                boys_rt_any<R>(C.L, T, F, a.boys_d, a.boys_f);
                 const R pref = bp.K * kp.K * rs;
                 R* cf = coef + lane * COOP_NCOEF;
                 cf[0] = bp.PA[0]; cf[1] = bp.PA[1]; cf[2] = bp.PA[2];
@@ -169,103 +276,7 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
             const int tt = lane + 32 * k;
             if (tt < C.nacc) V[C.N + tt] = acc[k];
         }
-        if (lane < 3) { hc[lane] = (R)B.AB[lane]; hc[3 + lane] = (R)K.AB[lane]; }
-        __syncwarp();
-        for (int g = 0; g < C.nhg; ++g) {
-            const int4 G = __ldg(C.hgrp + g);
-            if (lane < G.y) {
-                const int4 d = __ldg(C.hdesc + G.z + lane);
-                const int x0 = d.x & 0xffff, x1 = (unsigned)d.x >> 16;
-                const R v = (G.x == 0) ? fma(hc[d.w & 63], V[x1], V[x0]) : V[x0];
-                V[(unsigned)d.z >> 16] = v;
-            }
-            if (G.w) __syncwarp();
-        }
-        __syncwarp();
-
-        // ---- output-stationary digestion
-        R sdeg = R(1);
-        if (B.a == B.b) sdeg *= R(0.5);
-        if (K.a == K.b) sdeg *= R(0.5);
-        if (j == ib) sdeg *= R(0.5);
-        const int fa = B.bfa, fb = B.bfb, fc = K.bfa, fd = K.bfb;
-        const long long mb = B.mbase;
-        const int nJ = (a.want_j ? NA * NB + NC * ND : 0);
-        const int nK = (a.want_k ? NA * NC + NA * ND + NB * NC + NB * ND : 0);
-        for (int q = 0; q < a.nk; ++q) {
-            if (q > 0 && !a.want_k) break;
-            const double* Dq = a.D + (size_t)q * a.mstride;
-            double* Kq = a.K + (size_t)q * a.mstride;
-            // density blocks: ab, cd, bd, bc, ad, ac (each <= 36)
-            for (int e = lane; e < 216; e += 32) {
-                const int blk = e / 36, r = e - blk * 36;
-                int rr = 0, cc = 0, nr = 0, ncol = 0;
-                switch (blk) {
-                    case 0: nr = NA; ncol = NB; rr = fa; cc = fb; break;
-                    case 1: nr = NC; ncol = ND; rr = fc; cc = fd; break;
-                    case 2: nr = NB; ncol = ND; rr = fb; cc = fd; break;
-                    case 3: nr = NB; ncol = NC; rr = fb; cc = fc; break;
-                    case 4: nr = NA; ncol = ND; rr = fa; cc = fd; break;
-                    default: nr = NA; ncol = NC; rr = fa; cc = fc; break;
-                }
-                if (r < nr * ncol) Db[e] = ldR<R>(Dq + mb + (size_t)(rr + r / ncol) * n + cc + r % ncol);
-            }
-            __syncwarp();
-            const int nout = (q == 0 ? nJ : 0) + nK;
-            for (int o = lane; o < nout; o += 32) {
-                int kind = 0, oo = o;
-                if (q != 0) kind = 2;
-                if (q == 0 && oo >= nJ) { kind = 2; oo -= nJ; }
-                R sum = R(0);
-                double* dst;
-                double f;
-                if (kind == 0 && oo < NA * NB) {            // J'_ab
-                    const int m = oo / NB, k = oo % NB;
-                    for (int ls = 0; ls < NC * ND; ++ls) sum = fma(V[(m * NB + k) * NC * ND + ls], Db[36 + ls], sum);
-                    dst = a.J + mb + (size_t)(fa + m) * n + fb + k;
-                    f = 2.0 * (double)sdeg;
-                } else if (kind == 0) {                       // J'_cd
-                    oo -= NA * NB;
-                    const int l = oo / ND, s = oo % ND;
-                    for (int mk = 0; mk < NA * NB; ++mk) sum = fma(V[mk * NC * ND + l * ND + s], Db[mk], sum);
-                    dst = a.J + mb + (size_t)(fc + l) * n + fd + s;
-                    f = 2.0 * (double)sdeg;
-                } else if (oo < NA * NC) {                    // K'_ac += (ab|cd) D_bd
-                    const int m = oo / NC, l = oo % NC;
-                    for (int k = 0; k < NB; ++k)
-                        for (int s = 0; s < ND; ++s)
-                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[72 + k * ND + s], sum);
-                    dst = Kq + mb + (size_t)(fa + m) * n + fc + l;
-                    f = (double)sdeg;
-                } else if (oo < NA * NC + NA * ND) {          // K'_ad += (ab|cd) D_bc
-                    oo -= NA * NC;
-                    const int m = oo / ND, s = oo % ND;
-                    for (int k = 0; k < NB; ++k)
-                        for (int l = 0; l < NC; ++l)
-                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[108 + k * NC + l], sum);
-                    dst = Kq + mb + (size_t)(fa + m) * n + fd + s;
-                    f = (double)sdeg;
-                } else if (oo < NA * NC + NA * ND + NB * NC) {  // K'_bc += (ab|cd) D_ad
-                    oo -= NA * NC + NA * ND;
-                    const int k = oo / NC, l = oo % NC;
-                    for (int m = 0; m < NA; ++m)
-                        for (int s = 0; s < ND; ++s)
-                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[144 + m * ND + s], sum);
-                    dst = Kq + mb + (size_t)(fb + k) * n + fc + l;
-                    f = (double)sdeg;
-                } else {                                       // K'_bd += (ab|cd) D_ac
-                    oo -= NA * NC + NA * ND + NB * NC;
-                    const int k = oo / ND, s = oo % ND;
-                    for (int m = 0; m < NA; ++m)
-                        for (int l = 0; l < NC; ++l)
-                            sum = fma(V[((m * NB + k) * NC + l) * ND + s], Db[180 + m * NC + l], sum);
-                    dst = Kq + mb + (size_t)(fb + k) * n + fd + s;
-                    f = (double)sdeg;
-                }
-                atomicAdd(dst, f * (double)sum);
-            }
-            __syncwarp();
-        }
+        coop_hrr_digest<R>(C, V, Db, hc, B, K, ib, j, a, lane);
     }
     if (a.counters) {
 #pragma unroll

@@ -75,10 +75,19 @@ __global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ m
     Dmax[p] = (float)mx * 1.0000005f;
 }
 
+// X'_i + sgn X'_t of two fixed-point accumulator elements, summed as integers
+// and rounded once to FP64.
+__device__ __forceinline__ double fx_pair(const acc_t* __restrict__ X, size_t i, size_t t, bool minus)
+{
+    const long long hi_i = (long long)X[2 * i], lo_i = (long long)X[2 * i + 1];
+    const long long hi_t = (long long)X[2 * t], lo_t = (long long)X[2 * t + 1];
+    return minus ? fx_value(hi_i - hi_t, lo_i - lo_t) : fx_value(hi_i + hi_t, lo_i + lo_t);
+}
+
 // J = s s (J' + J'^T); K_q = s s (K'_q +/- K'_q^T), per slot, in the output layout.
 __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
                                 const int* __restrict__ mol_bfo, const double* __restrict__ sc,
-                                const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
+                                const acc_t* __restrict__ Jp, const acc_t* __restrict__ Kp, double* __restrict__ J,
                                 double* __restrict__ K, int want_j, int want_k)
 {
     const size_t slot = (size_t)ld * ld, ms = slot * nmol;
@@ -89,19 +98,19 @@ __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restric
     const size_t t = (size_t)m * slot + (size_t)c * ld + r;
     const int nm = mol_n[m];
     const double f = (r < nm && c < nm) ? sc[mol_bfo[m] + r] * sc[mol_bfo[m] + c] : 0.0;
-    if (want_j) J[i] = f * (Jp[i] + Jp[t]);
+    if (want_j) J[i] = f * fx_pair(Jp, i, t, false);
     if (!want_k) return;
     if (kind == CQ_DENS_REAL_SYM) {
-        K[i] = f * (Kp[i] + Kp[t]);
+        K[i] = f * fx_pair(Kp, i, t, false);
     } else if (kind == CQ_DENS_COMPLEX_HERM) {
-        K[2 * i] = f * (Kp[i] + Kp[t]);
-        K[2 * i + 1] = f * (Kp[ms + i] - Kp[ms + t]);
+        K[2 * i] = f * fx_pair(Kp, i, t, false);
+        K[2 * i + 1] = f * fx_pair(Kp + 2 * ms, i, t, true);
     } else {
         for (int I = 0; I < 4; ++I) {
-            const double* Kr = Kp + (2 * I) * ms;
-            const double* Ki = Kp + (2 * I + 1) * ms;
-            K[2 * (I * ms + i)] = f * (Kr[i] + Kr[t]);
-            K[2 * (I * ms + i) + 1] = f * (Ki[i] - Ki[t]);
+            const acc_t* Kr = Kp + 2 * (2 * I) * ms;
+            const acc_t* Ki = Kp + 2 * (2 * I + 1) * ms;
+            K[2 * (I * ms + i)] = f * fx_pair(Kr, i, t, false);
+            K[2 * (I * ms + i) + 1] = f * fx_pair(Ki, i, t, true);
         }
     }
 }
@@ -123,11 +132,12 @@ int ensure_scratch(cq_basis* b, int nk)
     const size_t nn = b->mstride;
     if (b->d_Dp) cudaFree(b->d_Dp);
     if (b->d_Kp) cudaFree(b->d_Kp);
-    b->d_Dp = b->d_Kp = nullptr;
+    b->d_Dp = nullptr;
+    b->d_Kp = nullptr;
     int rc;
     if ((rc = dalloc(&b->d_Dp, nn * nk))) return rc;
-    if ((rc = dalloc(&b->d_Kp, nn * nk))) return rc;
-    if (!b->d_Jp && (rc = dalloc(&b->d_Jp, nn))) return rc;
+    if ((rc = dalloc(&b->d_Kp, 2 * nn * nk))) return rc;
+    if (!b->d_Jp && (rc = dalloc(&b->d_Jp, 2 * nn))) return rc;
     if (!b->d_Dmax && (rc = dalloc(&b->d_Dmax, (size_t)b->nmol * b->lds * b->lds))) return rc;
     b->nk_cap = nk;
     return CQ_OK;
@@ -264,12 +274,6 @@ static int launch_passes(const cq_basis* b, JKArgs& a, ClassifyArgs c, const cq_
         const int Y = qc - X * (X + 1) / 2;
         a.ket_end = b->cls_off[Y + 1];
         a.same_class = (X == Y);
-        if (profile)
-            for (int pp = 0; pp < npp; ++pp) {
-                for (int e = 0; e < 2; ++e)
-                    if (!bm->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&bm->pev[qc][pp][e]));
-                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][0], s));
-            }
         for (int ta = t0; ta < t1;) {
             const long long base = b->task_cand[ta];
             int tb = (int)(std::upper_bound(b->task_cand.begin() + ta + 1, b->task_cand.begin() + t1 + 1, base + cap) -
@@ -296,17 +300,28 @@ static int launch_passes(const cq_basis* b, JKArgs& a, ClassifyArgs c, const cq_
                 a.qcount = b->d_qcount + 2 * qc + pp;
                 unsigned long long* base_cnt = a.counters;
                 a.counters = base_cnt + 4 * qc + 2 * pp;
+                cudaEvent_t* ev = nullptr;
+                if (profile) {   // one event pair per pass, summed by cq_fock_class_stats
+                    auto& v = bm->pev_pass[qc][pp];
+                    const int k = bm->pev_npass[qc][pp]++;
+                    while ((int)v.size() < 2 * (k + 1)) {
+                        cudaEvent_t e;
+                        CQ_CUDA(cudaEventCreate(&e));
+                        v.push_back(e);
+                    }
+                    ev = &v[2 * k];
+                    CQ_CUDA(cudaEventRecord(ev[0], s));
+                }
                 launch_jk_class(b, a, qc, pp, s);
+                if (profile) {
+                    CQ_CUDA(cudaEventRecord(ev[1], s));
+                    bm->pev_used[qc][pp] = true;
+                }
                 a.counters = base_cnt;
             }
             CQ_CUDA(cudaGetLastError());
             ta = tb;
         }
-        if (profile)
-            for (int pp = 0; pp < npp; ++pp) {
-                CQ_CUDA(cudaEventRecord(bm->pev[qc][pp][1], s));
-                bm->pev_used[qc][pp] = true;
-            }
     }
     return CQ_OK;
 }
@@ -386,9 +401,13 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
 
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s)
 {
+    if (b->variant[qc][fp32] == VARIANT_SYM && fp32 && SYM_LAUNCH[qc]) {
+        SYM_LAUNCH[qc](a, fp32, s);
+        return;
+    }
     // a class switched to the cooperative kernel uses it once its task list
     // has been rebuilt (by the next cq_fock_build); until then, lane groups
-    if (b->variant[qc][fp32] == VARIANT_COOP && b->passes) {
+    if (b->variant[qc][fp32] == VARIANT_COOP && b->coop_list && !b->coop_dirty) {
         JKArgs c = a;
         c.coop_list = 1;
         c.ntasks = (int)a.qmax;
@@ -438,9 +457,13 @@ extern "C" long long cq_get_list_capacity(void) { return g_list_capacity; }
 
 extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
 {
-    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1 || variant < 0 || variant > 1) {
+    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1 || variant < 0 || variant > 2) {
         set_error("cq_fock_set_variant: bad argument");
         return CQ_ERR_INVALID_ARG;
+    }
+    if (variant == VARIANT_SYM && (!fp32 || !SYM_LAUNCH[qc])) {
+        set_error("cq_fock_set_variant: this class and precision have no axis-permutation kernel");
+        return CQ_ERR_UNSUPPORTED;
     }
     if (b->variant[qc][fp32] != variant) b->coop_dirty = true;
     b->variant[qc][fp32] = variant;
@@ -502,10 +525,13 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
     dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
                                                               b->d_mol_bfo, b->d_bfo, nk, b->d_Dp, mol_mode,
                                                               b->d_Dmax);
-    CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, nn * sizeof(double), s));
-    CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, nn * nk * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, 2 * nn * sizeof(acc_t), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, 2 * nn * nk * sizeof(acc_t), s));
     CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
-    if (b->profile) memset(b->pev_used, 0, sizeof b->pev_used);
+    if (b->profile) {
+        memset(b->pev_used, 0, sizeof b->pev_used);
+        memset(b->pev_npass, 0, sizeof b->pev_npass);
+    }
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
@@ -571,9 +597,19 @@ extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, un
     if (prims) *prims = c[1];
     if (ms) {
         float t = 0.f;
-        if (b->profile && b->pev_used[qc][fp32])
-            CQ_CUDA(cudaEventElapsedTime(&t, b->pev[qc][fp32][0], b->pev[qc][fp32][1]));
-        *ms = t;
+        double tot = 0.0;
+        if (b->profile && b->pev_used[qc][fp32]) {
+            if (b->passes) {
+                for (int k = 0; k < b->pev_npass[qc][fp32]; ++k) {
+                    CQ_CUDA(cudaEventElapsedTime(&t, b->pev_pass[qc][fp32][2 * k], b->pev_pass[qc][fp32][2 * k + 1]));
+                    tot += t;
+                }
+            } else {
+                CQ_CUDA(cudaEventElapsedTime(&t, b->pev[qc][fp32][0], b->pev[qc][fp32][1]));
+                tot = t;
+            }
+        }
+        *ms = tot;
     }
     return CQ_OK;
 }
@@ -582,7 +618,7 @@ extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, un
 // density (one profiled build per variant after a warm-up build), keep the
 // fastest per class and precision.  Light classes (total angular momentum
 // below 4) stay on lane groups: one contracted quartet per warp cannot pay
-// off there.
+// off there.  The axis-permutation kernel exists for FP32 only.
 extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts, int* table,
                            double* ms_out, void* stream)
 {
@@ -597,20 +633,25 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     if ((rc = dalloc(&K, nn * (nk == 1 ? 1 : nk == 2 ? 2 : 8)))) { cudaFree(J); return rc; }
     const int old_profile = b->profile;
     b->profile = 1;
-    double best[NQC][2];
-    int choice[NQC][2];
+    constexpr int NV = 3;
+    double t[NQC][2][NV];
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p) { best[q][p] = 1e300; choice[q][p] = b->variant[q][p]; }
+        for (int p = 0; p < 2; ++p)
+            for (int v = 0; v < NV; ++v) t[q][p][v] = 1e300;
     auto Lof = [](int qc) {
         int X = 0;
         while ((X + 1) * (X + 2) / 2 <= qc) ++X;
         const int Y = qc - X * (X + 1) / 2;
         return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
     };
-    for (int v = 0; v < 2 && rc == CQ_OK; ++v) {
+    auto allowed = [&](int q, int p, int v) {
+        return v == VARIANT_LANES || (v == VARIANT_COOP && Lof(q) >= 4) ||
+               (v == VARIANT_SYM && p == 1 && SYM_LAUNCH[q] != nullptr);
+    };
+    for (int v = 0; v < NV && rc == CQ_OK; ++v) {
         for (int q = 0; q < NQC; ++q)
             for (int p = 0; p < 2; ++p) {
-                const int want = (Lof(q) >= 4) ? v : VARIANT_LANES;
+                const int want = allowed(q, p, v) ? v : VARIANT_LANES;
                 if (b->variant[q][p] != want) b->coop_dirty = true;
                 b->variant[q][p] = want;
             }
@@ -621,11 +662,11 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
         if (rc) break;
         for (int q = 0; q < NQC; ++q)
             for (int p = 0; p < 2; ++p) {
-                if (Lof(q) < 4 && v == VARIANT_COOP) continue;
+                if (!allowed(q, p, v)) continue;
                 double ms = 0.0;
                 unsigned long long nq = 0, np = 0;
                 if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &np))) break;
-                if (ms < best[q][p]) { best[q][p] = ms; choice[q][p] = v; }
+                t[q][p][v] = ms;
             }
     }
     b->profile = old_profile;
@@ -634,31 +675,40 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
         cudaFree(K);
         return rc;
     }
+    int best[NQC][2], second[NQC][2];
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < 2; ++p) {
-            if (b->variant[q][p] != choice[q][p]) b->coop_dirty = true;
-            b->variant[q][p] = choice[q][p];
+            best[q][p] = VARIANT_LANES;
+            second[q][p] = -1;
+            for (int v = 1; v < NV; ++v)
+                if (t[q][p][v] < t[q][p][best[q][p]]) best[q][p] = v;
+            for (int v = 0; v < NV; ++v)
+                if (v != best[q][p] && t[q][p][v] < 1e299 &&
+                    (second[q][p] < 0 || t[q][p][v] < t[q][p][second[q][p]]))
+                    second[q][p] = v;
+            if (b->variant[q][p] != best[q][p]) b->coop_dirty = true;
+            b->variant[q][p] = best[q][p];
         }
     // Refinement on the whole build: the class kernels of a build run
     // concurrently, so a variant that wins alone can lose beside the others.
-    // For the costliest classes, flip the variant and keep the flip only if
-    // the median time of three complete builds improves by more than 1 %.
+    // For the costliest classes, try the runner-up variant and keep it only
+    // if the median time of three complete builds improves by more than 1 %.
     auto build_ms = [&](double* out) -> int {
-        double t[3];
+        double tt[3];
         for (int r = 0; r < 3; ++r) {
             cq_fock_stats st;
             const int e = cq_fock_build(b, kind, P, J, K, &o, &st, stream);
             if (e) return e;
-            t[r] = st.ms;
+            tt[r] = st.ms;
         }
-        std::sort(t, t + 3);
-        *out = t[1];
+        std::sort(tt, tt + 3);
+        *out = tt[1];
         return CQ_OK;
     };
     std::vector<std::pair<double, int>> cand;
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++p)
-            if (Lof(q) >= 4 && best[q][p] < 1e299) cand.push_back({best[q][p], 2 * q + p});
+            if (second[q][p] >= 0) cand.push_back({t[q][p][best[q][p]], 2 * q + p});
     std::sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
         return x.first > y.first;
     });
@@ -667,14 +717,15 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     rc = build_ms(&cur);
     for (size_t i = 0; i < cand.size() && rc == CQ_OK; ++i) {
         const int q = cand[i].second / 2, p = cand[i].second % 2;
-        b->variant[q][p] ^= 1;
+        const int keep = b->variant[q][p];
+        b->variant[q][p] = second[q][p];
         b->coop_dirty = true;
-        double t = 0.0;
-        if ((rc = build_ms(&t))) break;
-        if (t < 0.99 * cur) {
-            cur = t;
+        double tb = 0.0;
+        if ((rc = build_ms(&tb))) break;
+        if (tb < 0.99 * cur) {
+            cur = tb;
         } else {
-            b->variant[q][p] ^= 1;
+            b->variant[q][p] = keep;
             b->coop_dirty = true;
         }
     }
@@ -684,7 +735,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < 2; ++p) {
             if (table) table[2 * q + p] = b->variant[q][p];
-            if (ms_out) ms_out[2 * q + p] = best[q][p] < 1e299 ? best[q][p] : 0.0;
+            if (ms_out) ms_out[2 * q + p] = t[q][p][best[q][p]] < 1e299 ? t[q][p][best[q][p]] : 0.0;
         }
     return ensure_coop_tasks(b);
 }

@@ -25,8 +25,10 @@ extern const LaunchSchwarz SCHWARZ_LAUNCH[NPC];
 void launch_coop(const JKArgs& a, int qc, int fp32, cudaStream_t s);
 size_t coop_smem_bytes(int qc, int fp32);
 
-// kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative
-constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1;
+// kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative,
+// 2 axis-permutation lane groups (FP32; classes with an entry in SYM_LAUNCH)
+constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1, VARIANT_SYM = 2;
+extern const LaunchJK SYM_LAUNCH[NQC];      // NULL where a class has no split kernel
 extern const int DEFAULT_VARIANT[NQC][2];
 
 void set_error(const std::string& msg);
@@ -99,8 +101,8 @@ struct cq_basis {
     // per-build scratch (grown on demand)
     int nk_cap = 0;
     double* d_Dp = nullptr;        // nk scaled densities
-    double* d_Jp = nullptr;        // J'
-    double* d_Kp = nullptr;        // nk K'
+    cq::acc_t* d_Jp = nullptr;     // J' (two fx_add words per element)
+    cq::acc_t* d_Kp = nullptr;     // nk K' (two fx_add words per element)
     float* d_Dmax = nullptr;       // nsh x nsh
     unsigned long long* d_cnt = nullptr;  // 4 totals + per class/precision (quartets, prims)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -108,6 +110,9 @@ struct cq_basis {
     int profile = 0;
     cudaEvent_t pev[cq::NQC][2][2] = {};
     bool pev_used[cq::NQC][2] = {};
+    // builds in passes: one event pair per pass and precision of a class
+    std::vector<cudaEvent_t> pev_pass[cq::NQC][2];
+    int pev_npass[cq::NQC][2] = {};
     unsigned long long pcnt[cq::NQC][2][2] = {};
     // dense drivers (SCF, RT): library handles and cached one-electron data
     void* blas = nullptr;          // cublasHandle_t
@@ -147,6 +152,7 @@ struct cq_basis {
     cudaEvent_t join_ev[NSIDE] = {};
     int4* d_coop_tasks = nullptr;
     bool coop_dirty = true;
+    bool coop_list = false;        // cooperative classes read the screened lists
     // large bases: one task per (class, bra pair) and a quartet list of
     // list_cap entries filled and drained in passes of whole tasks
     bool passes = false;
@@ -163,6 +169,9 @@ namespace cq {
 // (settable through cq_set_list_capacity)
 extern long long g_list_capacity;
 constexpr int COOP_CHUNK = 64;   // primitive quartets per cooperative task
+// candidate quartets of the cooperative classes above which the cooperative
+// kernel reads the screened lists instead of a per-candidate task table
+constexpr long long COOP_TASK_CANDIDATES = 4000000;
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s);
 int ensure_coop_tasks(cq_basis* b);
 int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, bool profile, cudaStream_t s,

@@ -28,8 +28,8 @@ struct JKArgs {
     int nbf;                      // leading dimension of every matrix slot
     long long mstride;            // elements of one matrix over all slots (density q at q * mstride)
     int want_j, want_k;
-    double* J;                    // J' accumulator nbf x nbf
-    double* K;                    // K' accumulators nk x nbf x nbf
+    acc_t* J;                     // J' accumulator nbf x nbf (fx_add words)
+    acc_t* K;                     // K' accumulators nk x nbf x nbf (fx_add words)
     const double* boys_d;
     const float* boys_f;
     unsigned long long* counters; // [0] quartets, [1] primitive quartets
@@ -67,15 +67,13 @@ __device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPair
     for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
 }
 
-// One primitive quartet: prefactor, Boys values and the class's vertical
-// recurrence, accumulated into acc.
-template <int LA, int LB, int LC, int LD, typename R>
-__device__ __forceinline__ void prim_quartet(const PrimPairT<R>& bp, const PrimPairT<R>& kp,
-                                             const R* __restrict__ boys_tab, R* __restrict__ acc)
+// Per-primitive-quartet quantities of the vertical recurrence: prefactor
+// times Boys values, PA, QC, W-P, W-Q and the exponent ratios.
+template <int L, typename R>
+__device__ __forceinline__ void prim_setup(const PrimPairT<R>& bp, const PrimPairT<R>& kp,
+                                           const double* __restrict__ boys_d, const float* __restrict__ boys_f,
+                                           PrimQuartet<R>& q)
 {
-    using C = EriClass<LA, LB, LC, LD>;
-    constexpr int L = LA + LB + LC + LD;
-    PrimQuartet<R> q;
     const R s = bp.zeta + kp.zeta;
     const R rs = rsqrt_r(s);
     const R is = rs * rs;
@@ -84,7 +82,7 @@ __device__ __forceinline__ void prim_quartet(const PrimPairT<R>& bp, const PrimP
     const R roe = bp.zeta * is;   // rho/eta  = zeta/(zeta+eta)
     const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
     R F[L + 1];
-    boys<L>(T, F, boys_tab);
+    boys_q<L>(T, F, boys_d, boys_f);
     const R pref = bp.K * kp.K * rs;
 #pragma unroll
     for (int m = 0; m <= L; ++m) q.S[m] = pref * F[m];
@@ -94,6 +92,18 @@ __device__ __forceinline__ void prim_quartet(const PrimPairT<R>& bp, const PrimP
     q.WQ[0] = roe * PQx;  q.WQ[1] = roe * PQy;  q.WQ[2] = roe * PQz;
     q.oo2z = bp.oo2z; q.oo2e = kp.oo2z; q.oo2ze = R(0.5) * is;
     q.roz = roz; q.roe = roe;
+}
+
+// One primitive quartet: prefactor, Boys values and the class's vertical
+// recurrence, accumulated into acc.
+template <int LA, int LB, int LC, int LD, typename R>
+__device__ __forceinline__ void prim_quartet(const PrimPairT<R>& bp, const PrimPairT<R>& kp,
+                                             const double* __restrict__ boys_d, const float* __restrict__ boys_f,
+                                             R* __restrict__ acc)
+{
+    using C = EriClass<LA, LB, LC, LD>;
+    PrimQuartet<R> q;
+    prim_setup<LA + LB + LC + LD, R>(bp, kp, boys_d, boys_f, q);
     C::template prim<R>(q, acc);
 }
 
@@ -106,15 +116,13 @@ __device__ __forceinline__ void eri_quartet(const PairHdr& B, const PairHdr& K, 
     R acc[C::NACC];
 #pragma unroll
     for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
-    const R* boys_tab;
-    if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
     for (int ip = 0; ip < B.nprim; ++ip) {
         PrimPairT<R> bp;
         load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
         for (int jp = 0; jp < K.nprim; ++jp) {
             PrimPairT<R> kp;
             load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-            prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
+            prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
         }
     }
     R ABv[3] = {(R)B.AB[0], (R)B.AB[1], (R)B.AB[2]};
@@ -171,13 +179,13 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
         for (int l = 0; l < NC; ++l)
 #pragma unroll
             for (int s = 0; s < ND; ++s)
-                atomicAdd(a.J + mb + (size_t)(fc + l) * n + fd + s, f * (double)jcd[l * ND + s]);
+                fx_add(a.J, mb + (size_t)(fc + l) * n + fd + s, f * (double)jcd[l * ND + s]);
     }
     if (a.want_k) {
 #pragma unroll 1
         for (int q = 0; q < a.nk; ++q) {
             const double* Dq = a.D + (size_t)q * a.mstride;
-            double* Kq = a.K + (size_t)q * a.mstride;
+            acc_t* Kq = a.K + 2 * (size_t)q * a.mstride;
             R dbd[NB * ND], dbc[NB * NC], dad[NA * ND], dac[NA * NC];
             R kac[NA * NC], kad[NA * ND], kbc[NB * NC], kbd[NB * ND];
 #pragma unroll
@@ -212,16 +220,16 @@ __device__ __forceinline__ void digest(const PairHdr& B, const PairHdr& K, const
 #pragma unroll
             for (int m = 0; m < NA; ++m) {
 #pragma unroll
-                for (int l = 0; l < NC; ++l) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fc + l, f * (double)kac[m * NC + l]);
+                for (int l = 0; l < NC; ++l) fx_add(Kq, mb + (size_t)(fa + m) * n + fc + l, f * (double)kac[m * NC + l]);
 #pragma unroll
-                for (int s = 0; s < ND; ++s) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fd + s, f * (double)kad[m * ND + s]);
+                for (int s = 0; s < ND; ++s) fx_add(Kq, mb + (size_t)(fa + m) * n + fd + s, f * (double)kad[m * ND + s]);
             }
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
 #pragma unroll
-                for (int l = 0; l < NC; ++l) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fc + l, f * (double)kbc[k * NC + l]);
+                for (int l = 0; l < NC; ++l) fx_add(Kq, mb + (size_t)(fb + k) * n + fc + l, f * (double)kbc[k * NC + l]);
 #pragma unroll
-                for (int s = 0; s < ND; ++s) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fd + s, f * (double)kbd[k * ND + s]);
+                for (int s = 0; s < ND; ++s) fx_add(Kq, mb + (size_t)(fb + k) * n + fd + s, f * (double)kbd[k * ND + s]);
             }
         }
     }
@@ -262,7 +270,7 @@ __device__ __forceinline__ void digest_part(const PairHdr& B, const PairHdr& K, 
                 t = fma(v, dcd[ls], t);
                 jcd[ls] = fma(v, dab, jcd[ls]);
             }
-            atomicAdd(a.J + mb + (size_t)(fa + m) * n + fb + k, 2.0 * (double)sdeg * (double)t);
+            fx_add(a.J, mb + (size_t)(fa + m) * n + fb + k, 2.0 * (double)sdeg * (double)t);
         }
     }
     if (a.want_k) {
@@ -355,15 +363,13 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
     for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
     unsigned long long nq = 0, np = 0;
     if (on) {
-        const R* boys_tab;
-        if constexpr (sizeof(R) == 8) boys_tab = (const R*)a.boys_d; else boys_tab = (const R*)a.boys_f;
         const int nkp = K.nprim, tot = B.nprim * K.nprim;
         for (int pq = sub; pq < tot; pq += G) {
             const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
             PrimPairT<R> bp, kp;
             load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
             load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-            prim_quartet<LA, LB, LC, LD, R>(bp, kp, boys_tab, acc);
+            prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
         }
         if (sub == 0) { nq = 1; np = (unsigned long long)tot; }
     }
@@ -410,7 +416,7 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
                     if (same[k]) v += u;
                 }
                 if (head && on && v != 0.0)
-                    atomicAdd(a.J + B.mbase + (size_t)(B.bfa + i / NB) * a.nbf + B.bfb + i % NB, v);
+                    fx_add(a.J, B.mbase + (size_t)(B.bfa + i / NB) * a.nbf + B.bfb + i % NB, v);
             }
         }
     } else {
@@ -440,11 +446,11 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
                     for (int s = 0; s < ND; ++s) {
                         const R v = group_sum<R, G>(jcd[l * ND + s]);
                         if (on && ((l * ND + s) % G) == sub)
-                            atomicAdd(a.J + mb + (size_t)(fc + l) * n + fd + s, f * (double)v);
+                            fx_add(a.J, mb + (size_t)(fc + l) * n + fd + s, f * (double)v);
                     }
             }
             if (a.want_k) {
-                double* Kq = a.K + (size_t)q * a.mstride;
+                acc_t* Kq = a.K + 2 * (size_t)q * a.mstride;
                 const double f = (double)sdeg;
                 int e2 = 0;
 #pragma unroll
@@ -452,28 +458,28 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
 #pragma unroll
                     for (int l = 0; l < NC; ++l, ++e2) {
                         const R v = group_sum<R, G>(kb[m * NC + l]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fc + l, f * (double)v);
+                        if (on && (e2 % G) == sub) fx_add(Kq, mb + (size_t)(fa + m) * n + fc + l, f * (double)v);
                     }
 #pragma unroll
                 for (int m = 0; m < NA; ++m)
 #pragma unroll
                     for (int s = 0; s < ND; ++s, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + m * ND + s]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fa + m) * n + fd + s, f * (double)v);
+                        if (on && (e2 % G) == sub) fx_add(Kq, mb + (size_t)(fa + m) * n + fd + s, f * (double)v);
                     }
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
 #pragma unroll
                     for (int l = 0; l < NC; ++l, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + NA * ND + k * NC + l]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fc + l, f * (double)v);
+                        if (on && (e2 % G) == sub) fx_add(Kq, mb + (size_t)(fb + k) * n + fc + l, f * (double)v);
                     }
 #pragma unroll
                 for (int k = 0; k < NB; ++k)
 #pragma unroll
                     for (int s = 0; s < ND; ++s, ++e2) {
                         const R v = group_sum<R, G>(kb[NA * NC + NA * ND + NB * NC + k * ND + s]);
-                        if (on && (e2 % G) == sub) atomicAdd(Kq + mb + (size_t)(fb + k) * n + fd + s, f * (double)v);
+                        if (on && (e2 % G) == sub) fx_add(Kq, mb + (size_t)(fb + k) * n + fd + s, f * (double)v);
                     }
             }
         }
@@ -503,17 +509,44 @@ __global__ void __launch_bounds__(JK_THREADS) jk_kernel(const JKArgs a)
         jk_chunk<LA, LB, LC, LD, R, G>(a, w, cnt);
 }
 
-// Schwarz factors of the pairs [begin, end) of class (LA LB): one thread per
-// pair, (ab|ab) in FP64.
-template <int LA, int LB>
-__global__ void schwarz_kernel(const JKArgs a, int begin, int end, float* Qf, double* Qd)
+// Schwarz factors of the pairs [begin, end) of class (LA LB): a group of G
+// lanes per pair splits its primitive quartets (ab|ab), the group sums the
+// accumulators with shuffles and its first lane runs the HRR and takes the
+// largest diagonal element, all in FP64.
+template <int LA, int LB, int G>
+__global__ void __launch_bounds__(JK_THREADS) schwarz_kernel(const JKArgs a, int begin, int end, float* Qf, double* Qd)
 {
     constexpr int NA = ncart(LA), NB = ncart(LB);
-    const int p = begin + blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= end) return;
-    const PairHdr B = a.pairs[p];
-    double I[EriClass<LA, LB, LA, LB>::N];
-    eri_quartet<LA, LB, LA, LB, double>(B, B, a, I);
+    using C = EriClass<LA, LB, LA, LB>;
+    const int lane = threadIdx.x & 31;
+    const int grp = lane / G, sub = lane - (lane / G) * G;
+    const long long w = ((long long)blockIdx.x * JK_THREADS + threadIdx.x) >> 5;
+    const long long p0 = begin + w * (32 / G);
+    if (p0 >= end) return;                       // whole warp past the end
+    const long long p = p0 + grp;
+    const bool on = p < end;
+    const PairHdr B = a.pairs[on ? p : p0];
+    double acc[C::NACC];
+#pragma unroll
+    for (int i = 0; i < C::NACC; ++i) acc[i] = 0.0;
+    if (on) {
+        const int tot = B.nprim * B.nprim;
+        for (int pq = sub; pq < tot; pq += G) {
+            const int ip = pq / B.nprim, jp = pq - (pq / B.nprim) * B.nprim;
+            PrimPairT<double> bp, kp;
+            load_prim<double>(a.prims, a.primsf, B.poff + ip, bp);
+            load_prim<double>(a.prims, a.primsf, B.poff + jp, kp);
+            prim_quartet<LA, LB, LA, LB, double>(bp, kp, a.boys_d, a.boys_f, acc);
+        }
+    }
+    if constexpr (G > 1) {
+#pragma unroll
+        for (int i = 0; i < C::NACC; ++i) acc[i] = group_sum<double, G>(acc[i]);
+    }
+    if (!on || sub != 0) return;
+    double I[C::N];
+    const double ABv[3] = {B.AB[0], B.AB[1], B.AB[2]};
+    C::template hrr<double>(acc, ABv, ABv, I);
     double mx = 0.0;
 #pragma unroll
     for (int m = 0; m < NA; ++m)

@@ -27,11 +27,14 @@ __global__ void dmax_kernel(int nmol, int ld, int lds, const int* __restrict__ m
                             float* __restrict__ Dmax);
 __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restrict__ mol_n,
                                 const int* __restrict__ mol_bfo, const double* __restrict__ sc,
-                                const double* __restrict__ Jp, const double* __restrict__ Kp, double* __restrict__ J,
+                                const acc_t* __restrict__ Jp, const acc_t* __restrict__ Kp, double* __restrict__ J,
                                 double* __restrict__ K, int want_j, int want_k);
 
-// Scratch of the allocation-free build: 16 MiB held by every device that
-// loads the library, for as long as the library stays loaded.
+// Scratch of the allocation-free build: 16 MiB on every device whose code
+// module for this file is loaded, held until the library is unloaded.  With
+// CUDA's lazy module loading the module is loaded (and the 16 MiB reserved)
+// by the first cudaGetSymbolAddress below, i.e. by the first call on a
+// device; eager loading reserves it when the library's code is loaded.
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(16) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
@@ -66,20 +69,23 @@ static int scratch_address(void** out)
 
 using namespace cq;
 
+// Single-molecule bases only: a batched basis needs nmol slots of its
+// largest molecule (noalloc_bytes below, which the call itself checks).
 extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
 {
     const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
     const size_t nn = (size_t)nbf * nbf;
-    return round256(nn * nk * sizeof(double)) * 2 + round256(nn * sizeof(double)) +
-           round256((size_t)nshell * nshell * sizeof(float)) + round256((4 + 6 * NQC) * sizeof(unsigned long long));
+    return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
+           round256(2 * nn * sizeof(acc_t)) + round256((size_t)nshell * nshell * sizeof(float)) +
+           round256((4 + 6 * NQC) * sizeof(unsigned long long));
 }
 
 static size_t noalloc_bytes(const cq_basis* b, int kind)
 {
     const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
     const size_t nn = b->mstride;
-    return round256(nn * nk * sizeof(double)) * 2 + round256(nn * sizeof(double)) +
-           round256((size_t)b->nmol * b->lds * b->lds * sizeof(float)) +
+    return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
+           round256(2 * nn * sizeof(acc_t)) + round256((size_t)b->nmol * b->lds * b->lds * sizeof(float)) +
            round256((4 + 6 * NQC) * sizeof(unsigned long long));
 }
 
@@ -116,8 +122,8 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     const size_t nn = b->mstride;
     unsigned char* p = (unsigned char*)base;
     double* Dp = (double*)p;          p += round256(nn * nk * sizeof(double));
-    double* Kp = (double*)p;          p += round256(nn * nk * sizeof(double));
-    double* Jp = (double*)p;          p += round256(nn * sizeof(double));
+    acc_t* Kp = (acc_t*)p;            p += round256(2 * nn * nk * sizeof(acc_t));
+    acc_t* Jp = (acc_t*)p;            p += round256(2 * nn * sizeof(acc_t));
     float* Dmax = (float*)p;          p += round256((size_t)b->nmol * b->lds * b->lds * sizeof(float));
     unsigned long long* cnt = (unsigned long long*)p;
 
@@ -128,8 +134,8 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     dmax_kernel<<<(unsigned)((nsl + 127) / 128), 128, 0, s>>>(b->nmol, n, b->lds, b->d_mol_nsh, b->d_mol_sho,
                                                               b->d_mol_bfo, b->d_bfo, nk, Dp, nullptr, Dmax);
     // the array keeps the previous call's contents: clear the accumulators
-    CQ_CUDA(cudaMemsetAsync(Jp, 0, nn * sizeof(double), s));
-    CQ_CUDA(cudaMemsetAsync(Kp, 0, nn * nk * sizeof(double), s));
+    CQ_CUDA(cudaMemsetAsync(Jp, 0, 2 * nn * sizeof(acc_t), s));
+    CQ_CUDA(cudaMemsetAsync(Kp, 0, 2 * nn * nk * sizeof(acc_t), s));
     CQ_CUDA(cudaMemsetAsync(cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
     JKArgs a;
     memset(&a, 0, sizeof a);

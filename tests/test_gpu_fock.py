@@ -148,15 +148,30 @@ def test_zero_density_and_screening(cq):
     assert st["quartets_fp64"] == 0
 
 
-@pytest.mark.parametrize("variant", [0, 1])
-def test_every_class_in_each_kernel_variant(cq, orc, variant):
-    """Lane-group (0) and warp-cooperative (1) kernels for all 21 classes,
-    FP64 and FP32 halves of the mixed build."""
-    mol, bas = CASES["OCNH3"]()
-    b = cq.Basis(mol, bas)
+def _set_all(cq, b, variant):
+    """Every class and precision to `variant` where it exists (the
+    axis-permutation kernel, 2, is FP32-only and for the high classes);
+    lane groups elsewhere."""
+    n = 0
     for qc in range(21):
         for p in (0, 1):
-            b.set_variant(qc, p, variant)
+            try:
+                b.set_variant(qc, p, variant)
+                n += variant == 2
+            except cq.CQError:
+                b.set_variant(qc, p, 0)
+    if variant == 2:
+        assert n == 8          # (dp|ds) (dp|pp) (dp|dp) (dd|ps) (dd|pp) (dd|ds) (dd|dp) (dd|dd)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_every_class_in_each_kernel_variant(cq, orc, variant):
+    """Lane-group (0), warp-cooperative (1) and axis-permutation (2, FP32)
+    kernels for all 21 classes, FP64 and FP32 halves of the mixed build,
+    and an almost all-FP32 build against the oracle."""
+    mol, bas = CASES["OCNH3"]()
+    b = cq.Basis(mol, bas)
+    _set_all(cq, b, variant)
     ob = orc.OBasis(mol, bas)
     P = synth.density(b.nbf, 9, 15, complex_=True)
     J, K = b.fock_build(_gpu(P))
@@ -167,6 +182,11 @@ def test_every_class_in_each_kernel_variant(cq, orc, variant):
     assert st["quartets_fp32"] > 0
     assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
     assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
+    # every quartet with bound below 10 in FP32 (FP32 rounding of O(1) values)
+    J3, K3, st3 = b.fock_build(_gpu(P), prec=cq.CQ_PREC_MIXED, mixed_tol=10.0, stats=True)
+    assert st3["quartets_fp32"] > 10 * st3["quartets_fp64"]
+    assert np.abs(J3.cpu().numpy() - Jo.real).max() < 2e-5
+    assert np.abs(K3.cpu().numpy() - Ko).max() < 2e-5
 
 
 def test_autotune_keeps_parity(cq, orc):
@@ -175,14 +195,15 @@ def test_autotune_keeps_parity(cq, orc):
     P = synth.density(b.nbf, 9, 16, complex_=True)
     tab = b.autotune(_gpu(P), cache=False)
     assert len(tab["variant"]) == 21
-    assert all(v in (0, 1) for row in tab["variant"] for v in row)
+    assert all(v in (0, 1, 2) for row in tab["variant"] for v in row)
+    assert all(row[0] != 2 for row in tab["variant"])      # FP32-only variant
     J, K = b.fock_build(_gpu(P))
     Jo, Ko = orc.jk(orc.OBasis(mol, bas), P)
     assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
     assert np.abs(K.cpu().numpy() - Ko).max() < TOL
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 def test_bounded_list_passes(cq, orc, variant):
     """A basis whose candidate quartets exceed the list capacity builds in
     passes (one task per bra pair, the cooperative kernel reading the list):
@@ -194,9 +215,7 @@ def test_bounded_list_passes(cq, orc, variant):
         b = cq.Basis(mol, bas)
     finally:
         cq.set_list_capacity(old)
-    for qc in range(21):
-        for p in (0, 1):
-            b.set_variant(qc, p, variant)
+    _set_all(cq, b, variant)
     ob = orc.OBasis(mol, bas)
     P = synth.density(b.nbf, 9, 17, complex_=True)
     J, K, st = b.fock_build(_gpu(P), stats=True)
@@ -210,3 +229,25 @@ def test_bounded_list_passes(cq, orc, variant):
     assert stm["quartets_fp32"] > 0
     assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
     assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_builds_bitwise_reproducible(cq, prec):
+    """J'/K' are accumulated as exact integers (order-independent), so two
+    identical builds -- class kernels on concurrent streams, atomics in any
+    order -- give bit-identical J and K, for every density kind."""
+    import torch
+    mol, bas = CASES["OCNH3"]()
+    b = cq.Basis(mol, bas)
+    n = b.nbf
+    Pp = np.stack([synth.hermitian_component(n, 40 + i, scale=0.1) for i in range(4)])
+    kw = {"prec": cq.CQ_PREC_MIXED, "mixed_tol": 1e-4} if prec == "mixed" else {}
+    for P in (synth.density(n, 9, 18), synth.density(n, 9, 19, complex_=True), Pp):
+        outs = [b.fock_build(_gpu(P), **kw) for _ in range(3)]
+        for J, K in outs[1:]:
+            assert torch.equal(J, outs[0][0])
+            assert torch.equal(K, outs[0][1])
+    # a second handle (other allocations, other stream timing) agrees too
+    b2 = cq.Basis(mol, bas)
+    J2, K2 = b2.fock_build(_gpu(P), **kw)
+    assert torch.equal(J2, outs[0][0]) and torch.equal(K2, outs[0][1])
