@@ -171,7 +171,8 @@ def test_axis_permutation_split_covers_every_target(cls):
 
 
 def test_axis_permutation_split_is_cheap():
-    """Per lane the split recurrence keeps about 1/G of the accumulators at
+    """Per lane the split recurrence keeps about 1/G of the accumulators (a
+    little more where orbits are smaller than the group) at
     a total cost (G lanes) of at most 1.25x (C3) or 1.6x (S3) the full one."""
     for cls in gen_sym.classes_for_sym():
         la, lb, lc, ld, G = cls
@@ -179,5 +180,5 @@ def test_axis_permutation_split_is_cheap():
         g.gen("R")
         full = g.flops
         _, st = gen_sym.emit_class(*cls)
-        assert st["n0"] <= st["nacc"] / G + 12
+        assert st["n0"] <= 1.2 * st["nacc"] / G + 12      # orbits with stabilisers are smaller
         assert G * (st["vrr_flops_lane"] - st["n0"]) <= (1.25 if G == 3 else 1.6) * full, (cls, st)
