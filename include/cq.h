@@ -205,10 +205,10 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
  * split one quartet's primitive quartets, generated straight-line
  * recurrences), 1 = warp-cooperative kernel (one warp per quartet walking
  * generated recurrence tables through shared memory), 2 = axis-permutation
- * lane groups (FP32 only, classes of total angular momentum >= 5 with a
- * d shell: 3 or 6 lanes per quartet each run the vertical recurrence for a
- * third or a sixth of the targets on axis-permuted inputs; CQ_ERR_UNSUPPORTED
- * elsewhere).  All give the same J/K to rounding; the choice only changes
+ * lane groups (classes of total angular momentum >= 4 with a d shell, and
+ * (pp|pp); FP64 too except (dd|dp) and (dd|dd): 3 or 6 lanes per quartet
+ * each run the vertical recurrence for a third or a sixth of the targets on
+ * axis-permuted inputs; CQ_ERR_UNSUPPORTED elsewhere).  All give the same J/K to rounding; the choice only changes
  * speed (set by the autotuner). */
 int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
 
@@ -229,7 +229,7 @@ int cq_set_list_capacity(long long entries);
 long long cq_get_list_capacity(void);
 
 /* Autotuner: times every kernel variant a class has (the cooperative one
- * for total angular momentum >= 4, the axis-permutation one in FP32 where it
+ * for total angular momentum >= 4, the axis-permutation one where it
  * exists; lighter classes keep lane groups) on the given density
  * (device, layout as for cq_fock_build) with the given options (NULL:
  * mixed precision, mixed_tol 1e-3), keeps the fastest variant per class and

@@ -31,6 +31,10 @@ LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
          "2120": 2, "2111": 2, "2210": 2, "1111": 2}
 
 
+# axis-permutation kernels: lanes per frame splitting the primitive quartets
+# (FP64 lists are the short, large-bound part of a mixed build)
+SYM_H_F32, SYM_H_F64 = 1, 2
+
 # lanes per shell pair in the Schwarz kernel, by la + lb: the (ab|ab)
 # quartets of one pair have up to MAX_PRIM^4 primitive quartets
 SCHWARZ_LANES = {0: 4, 1: 8, 2: 8, 3: 16, 4: 32}
@@ -123,22 +127,23 @@ def gen_sources():
         if not os.path.exists(path) or open(path).read() != code:
             with open(path, "w") as fh:
                 fh.write(code)
-        sym[cls] = G
-        write(os.path.join(GEN, f"cls_{cls}_sym.cu"), [
-            f"// generated by build.py: class ({cls}), FP32 axis-permutation kernel",
+        f64 = gen_sym.sym_fp64(la, lb, lc, ld)
+        sym[cls] = (G, f64)
+        lines = [
+            f"// generated by build.py: class ({cls}), axis-permutation kernel",
             '#include "cq_internal.h"',
             '#include "cq_coop.cuh"',
             '#include "coop_tables.cuh"',
             '#include "cq_sym.cuh"',
             "namespace cq {",
             f'#include "sym_{cls}.cuh"',
-            f"void launch_sym_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
+            "template <typename R, int H>",
+            f"static void launch_sym_{cls}_t(const JKArgs& a, cudaStream_t s)",
             "{",
-            "    if (!fp32) return;",
-            f"    constexpr int qc = {qc_of[cls]}, G = {G}, NGRP = 32 / G, WARPS = SYM_THREADS / 32;",
+            f"    constexpr int qc = {qc_of[cls]}, G = {G}, NGRP = 32 / (G * H), WARPS = SYM_THREADS / 32;",
             "    const int nslots = COOP_SIZES[qc].nslots;",
-            "    const size_t bytes = (size_t)WARPS * sym_warp_bytes<float>(nslots);",
-            f"    auto kern = jk_sym_kernel<{la}, {lb}, {lc}, {ld}, float, G>;",
+            "    const size_t bytes = (size_t)WARPS * sym_warp_bytes<R>(nslots);",
+            f"    auto kern = jk_sym_kernel<{la}, {lb}, {lc}, {ld}, R, G, H>;",
             "    static int attr_done = 0;",
             "    if (!attr_done) {",
             "        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);",
@@ -150,7 +155,13 @@ def gen_sources():
             "    if (blocks > jk_grid_cap()) blocks = jk_grid_cap();",
             "    kern<<<(unsigned)blocks, SYM_THREADS, bytes, s>>>(a, qc, nslots);",
             "}",
-            "}  // namespace cq"])
+            f"void launch_sym_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
+            "{",
+            f"    if (fp32) launch_sym_{cls}_t<float, {SYM_H_F32}>(a, s);"]
+        if f64:
+            lines.append(f"    else launch_sym_{cls}_t<double, {SYM_H_F64}>(a, s);")
+        lines += ["}", "}  // namespace cq"]
+        write(os.path.join(GEN, f"cls_{cls}_sym.cu"), lines)
     # dispatch table of the split kernels (NULL where a class has none)
     d = ['#include "cq_internal.h"', "namespace cq {"]
     for cls in sym:
@@ -160,6 +171,11 @@ def gen_sources():
         c = f"{X[0]}{X[1]}{Y[0]}{Y[1]}"
         entries.append(f"launch_sym_{c}" if c in sym else "nullptr")
     d.append("const LaunchJK SYM_LAUNCH[NQC] = {" + ", ".join(entries) + "};")
+    f64s = []
+    for (X, Y) in qclasses():
+        c = f"{X[0]}{X[1]}{Y[0]}{Y[1]}"
+        f64s.append("1" if c in sym and sym[c][1] else "0")
+    d.append("const int SYM_F64[NQC] = {" + ", ".join(f64s) + "};")
     d.append("}  // namespace cq")
     write(os.path.join(GEN, "cq_dispatch_split.cu"), d)
     sys.path.remove(CSRC)

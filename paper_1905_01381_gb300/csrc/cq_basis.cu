@@ -133,10 +133,12 @@ __global__ void pair_prep_kernel(int npair, const PairHdr* pairs, const double* 
                 o.PA[x] = o.P[x] - A[x];
             }
             o.K = coef[poff[h.a] + i] * coef[poff[h.b] + j] * exp(-a * b / z * AB2) * kfac / z;
+            o.pad[0] = o.pad[1] = o.pad[2] = 0.0;
             out[q] = o;
             PrimPairF f;
             f.zeta = (float)o.zeta; f.oo2z = (float)o.oo2z; f.K = (float)o.K;
             for (int x = 0; x < 3; ++x) { f.P[x] = (float)o.P[x]; f.PA[x] = (float)o.PA[x]; }
+            f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
             outf[q] = f;
         }
 }

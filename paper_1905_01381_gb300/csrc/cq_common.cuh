@@ -16,8 +16,9 @@ __host__ __device__ constexpr int ncart(int L) { return (L + 1) * (L + 2) / 2; }
 //   PA = P - A, K = c_a c_b exp(-alpha beta/zeta |A-B|^2) * sqrt(2) pi^{5/4} / zeta
 // so that the (ss|ss)^(m) prefactor is K_ab K_cd / sqrt(zeta + eta).
 template <typename R>
-struct PrimPairT {
+struct __align__(16) PrimPairT {
     R zeta, oo2z, P[3], PA[3], K;
+    R pad[3];   // 12 values: loaded as three 16-byte (FP32) or six 16-byte (FP64) vectors
 };
 using PrimPair = PrimPairT<double>;
 using PrimPairF = PrimPairT<float>;

@@ -401,7 +401,7 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
 
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s)
 {
-    if (b->variant[qc][fp32] == VARIANT_SYM && fp32 && SYM_LAUNCH[qc]) {
+    if (b->variant[qc][fp32] == VARIANT_SYM && SYM_LAUNCH[qc] && (fp32 || SYM_F64[qc])) {
         SYM_LAUNCH[qc](a, fp32, s);
         return;
     }
@@ -461,7 +461,7 @@ extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
         set_error("cq_fock_set_variant: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
-    if (variant == VARIANT_SYM && (!fp32 || !SYM_LAUNCH[qc])) {
+    if (variant == VARIANT_SYM && (!SYM_LAUNCH[qc] || (!fp32 && !SYM_F64[qc]))) {
         set_error("cq_fock_set_variant: this class and precision have no axis-permutation kernel");
         return CQ_ERR_UNSUPPORTED;
     }
@@ -618,7 +618,8 @@ extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, un
 // density (one profiled build per variant after a warm-up build), keep the
 // fastest per class and precision.  Light classes (total angular momentum
 // below 4) stay on lane groups: one contracted quartet per warp cannot pay
-// off there.  The axis-permutation kernel exists for FP32 only.
+// off there.  The axis-permutation kernel exists for the classes listed in
+// SYM_LAUNCH (FP64 where SYM_F64).
 extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts, int* table,
                            double* ms_out, void* stream)
 {
@@ -646,7 +647,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     };
     auto allowed = [&](int q, int p, int v) {
         return v == VARIANT_LANES || (v == VARIANT_COOP && Lof(q) >= 4) ||
-               (v == VARIANT_SYM && p == 1 && SYM_LAUNCH[q] != nullptr);
+               (v == VARIANT_SYM && SYM_LAUNCH[q] != nullptr && (p == 1 || SYM_F64[q]));
     };
     for (int v = 0; v < NV && rc == CQ_OK; ++v) {
         for (int q = 0; q < NQC; ++q)

@@ -26,9 +26,11 @@ void launch_coop(const JKArgs& a, int qc, int fp32, cudaStream_t s);
 size_t coop_smem_bytes(int qc, int fp32);
 
 // kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative,
-// 2 axis-permutation lane groups (FP32; classes with an entry in SYM_LAUNCH)
+// 2 axis-permutation lane groups (classes with an entry in SYM_LAUNCH; FP64
+// where SYM_F64)
 constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1, VARIANT_SYM = 2;
 extern const LaunchJK SYM_LAUNCH[NQC];      // NULL where a class has no split kernel
+extern const int SYM_F64[NQC];              // 1 where the split kernel also exists in FP64
 extern const int DEFAULT_VARIANT[NQC][2];
 
 void set_error(const std::string& msg);

@@ -49,22 +49,31 @@ template <typename R>
 __device__ __forceinline__ void load_prim(const PrimPair* pd, const PrimPairF* pf, int i,
                                           PrimPairT<R>& o);
 
+// The pair data of a primitive pair in 16-byte vector loads (a lane reads
+// its own pair, so the loads of a warp are scattered: fewer, wider loads
+// cost fewer L1 wavefronts).
 template <>
 __device__ __forceinline__ void load_prim<double>(const PrimPair* pd, const PrimPairF*, int i,
                                                   PrimPairT<double>& o)
 {
-    const double* s = reinterpret_cast<const double*>(pd + i);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
+    const double2* s = reinterpret_cast<const double2*>(pd + i);
+    const double2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3);
+    o.zeta = a.x; o.oo2z = a.y;
+    o.P[0] = b.x; o.P[1] = b.y; o.P[2] = c.x;
+    o.PA[0] = c.y; o.PA[1] = d.x; o.PA[2] = d.y;
+    o.K = __ldg(reinterpret_cast<const double*>(s + 4));
 }
 
 template <>
 __device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPairF* pf, int i,
                                                  PrimPairT<float>& o)
 {
-    const float* s = reinterpret_cast<const float*>(pf + i);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) (&o.zeta)[k] = __ldg(s + k);
+    const float4* s = reinterpret_cast<const float4*>(pf + i);
+    const float4 a = __ldg(s), b = __ldg(s + 1);
+    o.zeta = a.x; o.oo2z = a.y;
+    o.P[0] = a.z; o.P[1] = a.w; o.P[2] = b.x;
+    o.PA[0] = b.y; o.PA[1] = b.z; o.PA[2] = b.w;
+    o.K = __ldg(reinterpret_cast<const float*>(s + 2));
 }
 
 // Per-primitive-quartet quantities of the vertical recurrence: prefactor
@@ -364,12 +373,28 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
     unsigned long long nq = 0, np = 0;
     if (on) {
         const int nkp = K.nprim, tot = B.nprim * K.nprim;
-        for (int pq = sub; pq < tot; pq += G) {
-            const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
-            PrimPairT<R> bp, kp;
-            load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
-            load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-            prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
+        if constexpr (G == 1) {
+            for (int ip = 0; ip < B.nprim; ++ip) {
+                PrimPairT<R> bp;
+                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+                for (int jp = 0; jp < nkp; ++jp) {
+                    PrimPairT<R> kp;
+                    load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                    prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
+                }
+            }
+        } else {
+            // primitive quartets sub, sub + G, ... of the ip-major order
+            int ip = 0, jp = sub;
+            while (jp >= nkp) { jp -= nkp; ++ip; }
+            for (int pq = sub; pq < tot; pq += G) {
+                PrimPairT<R> bp, kp;
+                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
+                jp += G;
+                while (jp >= nkp) { jp -= nkp; ++ip; }
+            }
         }
         if (sub == 0) { nq = 1; np = (unsigned long long)tot; }
     }

@@ -30,6 +30,9 @@ __host__ __device__ constexpr size_t sym_warp_bytes(int nslots)
 
 // Primitive pair i with its vector components permuted: component x of the
 // result is component p[x] of the stored pair.
+// Primitive pair i with its vector components permuted: component x of the
+// result is component p[x] of the stored pair (scalar loads at permuted
+// offsets; cheaper here than vector loads followed by selects).
 template <typename R>
 __device__ __forceinline__ void load_prim_perm(const PrimPair* pd, const PrimPairF* pf, int i, int p0, int p1,
                                                int p2, PrimPairT<R>& o)
@@ -44,16 +47,24 @@ __device__ __forceinline__ void load_prim_perm(const PrimPair* pd, const PrimPai
     o.K = __ldg(s + 8);
 }
 
-template <int LA, int LB, int LC, int LD, typename R, int G>
+// H > 1: each of the G frames of a quartet is further split over H lanes
+// that take every H-th primitive quartet; their accumulators are summed
+// with shuffles before the scatter (more, shorter work units for short
+// lists).  Lane r of a group of G*H: frame k = r % G, primitive stride
+// offset h = r / G.
+template <int LA, int LB, int LC, int LD, typename R, int G, int H>
 __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int qc, int nslots)
 {
     using S = SymClass<LA, LB, LC, LD, G>;
     constexpr int L = LA + LB + LC + LD;
-    constexpr int NGRP = 32 / G;                 // groups per warp; lanes NGRP*G..31 idle in the recurrence
+    constexpr int GH = G * H;
+    constexpr int NGRP = 32 / GH;                // groups per warp; lanes NGRP*GH..31 idle in the recurrence
     constexpr int WARPS = SYM_THREADS / 32;
+    static_assert((H & (H - 1)) == 0 && NGRP >= 1, "H must be a power of two with G*H <= 32");
     const CoopClass C = COOP_CLASSES_D[qc];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int grp = lane / G, k = lane - (lane / G) * G;
+    const int grp = lane / GH, r = lane - (lane / GH) * GH;
+    const int k = r % G, h = r / G;
     const bool lane_on = grp < NGRP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* V = reinterpret_cast<R*>(smem_raw + (size_t)wib * sym_warp_bytes<R>(nslots));
@@ -76,25 +87,50 @@ __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int
             const int2 e = a.qlist[idx * a.qdir];
             const PairHdr B = a.pairs[e.x];
             const PairHdr K = a.pairs[e.y];
-            for (int ip = 0; ip < B.nprim; ++ip) {
-                PrimPairT<R> bp;
-                load_prim_perm<R>(a.prims, a.primsf, B.poff + ip, p0, p1, p2, bp);
-                for (int jp = 0; jp < K.nprim; ++jp) {
-                    PrimPairT<R> kp;
+            if constexpr (H == 1) {
+                for (int ip = 0; ip < B.nprim; ++ip) {
+                    PrimPairT<R> bp;
+                    load_prim_perm<R>(a.prims, a.primsf, B.poff + ip, p0, p1, p2, bp);
+                    for (int jp = 0; jp < K.nprim; ++jp) {
+                        PrimPairT<R> kp;
+                        load_prim_perm<R>(a.prims, a.primsf, K.poff + jp, p0, p1, p2, kp);
+                        PrimQuartet<R> q;
+                        prim_setup<L, R>(bp, kp, a.boys_d, a.boys_f, q);
+                        S::template prim<R>(q, acc);
+                    }
+                }
+            } else {
+                const int nkp = K.nprim, tot = B.nprim * nkp;
+                int ip = 0, jp = h;
+                while (jp >= nkp) { jp -= nkp; ++ip; }
+                for (int pq = h; pq < tot; pq += H) {
+                    PrimPairT<R> bp, kp;
+                    load_prim_perm<R>(a.prims, a.primsf, B.poff + ip, p0, p1, p2, bp);
                     load_prim_perm<R>(a.prims, a.primsf, K.poff + jp, p0, p1, p2, kp);
                     PrimQuartet<R> q;
                     prim_setup<L, R>(bp, kp, a.boys_d, a.boys_f, q);
                     S::template prim<R>(q, acc);
+                    jp += H;
+                    while (jp >= nkp) { jp -= nkp; ++ip; }
                 }
             }
-            if (k == 0) { nq += 1; np += (unsigned long long)B.nprim * K.nprim; }
+            if (r == 0) { nq += 1; np += (unsigned long long)B.nprim * K.nprim; }
+        }
+        if constexpr (H > 1) {   // sum the H partial accumulators of each frame into h = 0
+#pragma unroll
+            for (int i = 0; i < S::N0; ++i) {
+                R v = acc[i];
+#pragma unroll
+                for (int o = H / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, G * o);
+                acc[i] = v;
+            }
         }
         // the warp's quartets, one at a time: scatter the group's
         // accumulators into the [e0|f0] block, HRR and digestion
         for (int g = 0; g < NGRP; ++g) {
             const long long gi = w * NGRP + g;
             if (gi >= cnt) break;                    // warp-uniform
-            if (grp == g) {
+            if (grp == g && h == 0) {
 #pragma unroll
                 for (int i = 0; i < S::N0; ++i) {
                     const int d = __ldg(dst + i);

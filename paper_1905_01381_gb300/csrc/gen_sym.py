@@ -191,9 +191,18 @@ def check_plan(la, lb, lc, ld, G, rng):
 
 
 def classes_for_sym():
-    """(la, lb, lc, ld, G) of the classes that get the split kernel."""
-    return [(2, 1, 2, 0, 3), (2, 1, 1, 1, 3), (2, 2, 1, 0, 3), (2, 2, 1, 1, 3), (2, 2, 2, 0, 3),
-            (2, 1, 2, 1, 3), (2, 2, 2, 1, 3), (2, 2, 2, 2, 6)]
+    """(la, lb, lc, ld, G) of the classes that get the split kernel: every
+    class of total angular momentum >= 4 but (ps|ps)-like light ones; the
+    six-lane split where the three-lane one would not fit the registers."""
+    return [(1, 1, 1, 1, 3), (2, 0, 1, 1, 3), (2, 0, 2, 0, 3), (2, 1, 1, 0, 3), (2, 2, 0, 0, 3),
+            (2, 1, 2, 0, 3), (2, 1, 1, 1, 3), (2, 2, 1, 0, 3), (2, 2, 1, 1, 3), (2, 2, 2, 0, 3),
+            (2, 1, 2, 1, 3), (2, 2, 2, 1, 6), (2, 2, 2, 2, 6)]
+
+
+def sym_fp64(la, lb, lc, ld):
+    """Whether the split kernel is also built in FP64 (not for (dd|dp) and
+    (dd|dd), whose per-lane accumulators would not fit as doubles)."""
+    return (la, lb, lc, ld) not in ((2, 2, 2, 1), (2, 2, 2, 2))
 
 
 if __name__ == "__main__":

@@ -150,8 +150,9 @@ def test_zero_density_and_screening(cq):
 
 def _set_all(cq, b, variant):
     """Every class and precision to `variant` where it exists (the
-    axis-permutation kernel, 2, is FP32-only and for the high classes);
-    lane groups elsewhere."""
+    axis-permutation kernel, 2, exists for the classes of total angular
+    momentum >= 4 with a d shell and for (pp|pp), in FP64 too except (dd|dp)
+    and (dd|dd)); lane groups elsewhere."""
     n = 0
     for qc in range(21):
         for p in (0, 1):
@@ -161,12 +162,12 @@ def _set_all(cq, b, variant):
             except cq.CQError:
                 b.set_variant(qc, p, 0)
     if variant == 2:
-        assert n == 8          # (dp|ds) (dp|pp) (dp|dp) (dd|ps) (dd|pp) (dd|ds) (dd|dp) (dd|dd)
+        assert n == 13 + 11
 
 
 @pytest.mark.parametrize("variant", [0, 1, 2])
 def test_every_class_in_each_kernel_variant(cq, orc, variant):
-    """Lane-group (0), warp-cooperative (1) and axis-permutation (2, FP32)
+    """Lane-group (0), warp-cooperative (1) and axis-permutation (2)
     kernels for all 21 classes, FP64 and FP32 halves of the mixed build,
     and an almost all-FP32 build against the oracle."""
     mol, bas = CASES["OCNH3"]()
@@ -196,7 +197,7 @@ def test_autotune_keeps_parity(cq, orc):
     tab = b.autotune(_gpu(P), cache=False)
     assert len(tab["variant"]) == 21
     assert all(v in (0, 1, 2) for row in tab["variant"] for v in row)
-    assert all(row[0] != 2 for row in tab["variant"])      # FP32-only variant
+    assert tab["variant"][19][0] != 2 and tab["variant"][20][0] != 2   # FP32-only there
     J, K = b.fock_build(_gpu(P))
     Jo, Ko = orc.jk(orc.OBasis(mol, bas), P)
     assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
