@@ -9,7 +9,9 @@ kernel, density preparation and finalisation), Schwarz threshold 1e-14.
 Headline `value`: mixed-precision builds/s (FP32 for quartets whose Schwarz x
 density bound is below mixed_tol, everything accumulated in FP64), with the
 energy error against the all-FP64 GPU build checked in the same run
-(|dE| <= 1e-6 Eh).  The all-FP64 rate is reported beside it.
+(|dE| <= 1e-6 Eh).  The all-FP64 rate is reported beside it.  The same run
+then times the 100-atom, 1930-function single build (split FP32/FP64,
+Schwarz 1e-12) under the key "large100" (--large-steps, 0 to skip).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
   python bench.py --impl reference ...   # the CPU oracle on the same workload
@@ -48,6 +50,100 @@ def workload():
     n = bas.nbf
     P = synth.density(n, NOCC, 5, complex_=True)
     return mol, bas, P
+
+
+# the large single J/K build: 100-atom cluster, split FP32/FP64 precision
+LARGE_WORKLOAD = ("large100: 100-atom cluster (H with p 0.25, else C/N/O), 1930 Cartesian s,p,d functions, "
+                  "real P of 200 random orthonormal orbitals, Schwarz 1e-12")
+LARGE_MIXED_TOL = 3e-3
+LARGE_SCHWARZ = 1e-12
+
+
+def large_workload():
+    mol, bas = synth.workload_large100()
+    return mol, bas, synth.density(bas.nbf, 200, 11)
+
+
+def large_leg(steps: int, warmup: int, fp64_ref: bool):
+    """Config 3 in the same process: mixed builds timed with CUDA events
+    (one profiled build gives the per-class kernel times), optionally the
+    all-FP64 build for the energy error of the split."""
+    import torch
+
+    import paper_1905_01381_gb300 as cq
+    from paper_1905_01381_gb300 import flops as fl
+    mol, bas, Ph = large_workload()
+    t0 = time.perf_counter()
+    b = cq.Basis(mol, bas)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    n = b.nbf
+    P = torch.as_tensor(Ph, device="cuda")
+    J = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    K = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=LARGE_MIXED_TOL, schwarz_tol=LARGE_SCHWARZ, J=J, K=K)
+    for _ in range(warmup):
+        b.fock_build(P, **kw)
+    torch.cuda.synchronize()
+    tms = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for i in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.fock_build(P, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+    # one profiled build: per class and precision kernel times (the passes of
+    # a large basis run on one stream, so the events time each launch alone)
+    b.profile(True)
+    Jm, Km, st = b.fock_build(P, stats=True, **kw)
+    cls = b.class_stats()
+    b.profile(False)
+    peak64, peak32 = cq.peak_fma(False), cq.peak_fma(True)
+    dom = None
+    f64 = f32 = 0.0
+    for key, v in cls.items():
+        X, Y = cq.QUARTET_CLASSES[v["qc"]]
+        v["flops"] = fl.class_flops(X, Y, v["quartets"], v["prims"], 1)
+        if v["fp32"]:
+            f32 += v["flops"]
+        else:
+            f64 += v["flops"]
+        if dom is None or v["ms"] > cls[dom]["ms"]:
+            dom = key
+    dv = cls[dom]
+    dpeak = peak32 if dv["fp32"] else peak64
+    ms = sum(tms) / len(tms)
+    out = {"workload": LARGE_WORKLOAD, "nbf": n, "nshell": b.nshell, "basis_setup_s": setup_s,
+           "mixed_tol": LARGE_MIXED_TOL, "schwarz_tol": LARGE_SCHWARZ, "steps": steps, "warmup": warmup,
+           "builds_per_s": 1e3 / ms, "ms_per_build": ms,
+           "quartets_per_s": (st["quartets_fp64"] + st["quartets_fp32"]) * 1e3 / ms,
+           "quartets_per_build": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"]},
+           "prim_quartets_per_build": {"fp64": st["prim_fp64"], "fp32": st["prim_fp32"]},
+           "gflops_per_build": {"fp64": f64 * 1e-9, "fp32": f32 * 1e-9},
+           "build_roofline": {"min_ms": (f64 / peak64 + f32 / peak32) * 1e3, "ms": ms,
+                              "frac": (f64 / peak64 + f32 / peak32) * 1e3 / ms},
+           "roofline": {"bound": "alu", "kernel": dom, "achieved": dv["flops"] / (dv["ms"] * 1e-3) * 1e-12,
+                        "peak": dpeak * 1e-12, "unit": "TFLOP/s",
+                        "frac": dv["flops"] / (dv["ms"] * 1e-3) / dpeak, "traffic": None},
+           "class_roofline": {k: {"ms": round(v["ms"], 2), "quartets": v["quartets"], "prims": v["prims"],
+                                  "frac": round(v["flops"] / max(v["ms"], 1e-9) * 1e3
+                                                / (peak32 if v["fp32"] else peak64), 4)}
+                              for k, v in sorted(cls.items(), key=lambda kv: -kv[1]["ms"])},
+           "clocks": clk.summary(), "accuracy_vs_fp64_gpu": None}
+    if fp64_ref:
+        t = time.perf_counter()
+        J64, K64, st64 = b.fock_build(P, schwarz_tol=LARGE_SCHWARZ, stats=True)
+        torch.cuda.synchronize()
+        dE = float(torch.sum((2 * (Jm - J64) - (Km - K64)) * P.T).item())
+        out["accuracy_vs_fp64_gpu"] = {"dE_Eh": abs(dE), "max_dJ": float((Jm - J64).abs().max().item()),
+                                       "max_dK": float((Km - K64).abs().max().item()),
+                                       "fp64_build_s": time.perf_counter() - t,
+                                       "fp64_prim_quartets": st64["prim_fp64"]}
+    b.close()
+    return out
 
 
 def max_over_ranks(x: float, device) -> float:
@@ -228,7 +324,8 @@ def cpu_baseline(seconds: float, ref_frac: float):
 
 # ---------------------------------------------------------------- GPU arm
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic_jk_rt16.json")
-KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "gen_eri.py", "gen_coop.py")
+KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "cq_sym.cuh", "gen_eri.py",
+                  "gen_coop.py", "gen_sym.py")
 
 
 def kernel_sources_sha1():
@@ -425,6 +522,9 @@ def run_gpu(args):
         dist.destroy_process_group()
     if rk == 0 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, args.ref_frac) if ws == 1 else None
+    if rk == 0 and ws == 1 and args.large_steps > 0:
+        # the 100-atom single build (config 3) in the same run, under its own key
+        out["large100"] = large_leg(args.large_steps, args.large_warmup, args.large_fp64)
     if rk == 0:
         print(json.dumps(out))
     return 0
@@ -677,6 +777,11 @@ def main():
     ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch", "tolsweep"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
                          "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")
+    ap.add_argument("--large-steps", type=int, default=1,
+                    help="timed mixed builds of the 100-atom configuration after the headline (0: skip)")
+    ap.add_argument("--large-warmup", type=int, default=0)
+    ap.add_argument("--large-fp64", action="store_true",
+                    help="also build the 100-atom case in all-FP64 for the split's energy error (about an hour)")
     ap.add_argument("--rt-steps", type=int, default=100)
     ap.add_argument("--nmol", type=int, default=512)
     ap.add_argument("--ntrain", type=int, default=512)

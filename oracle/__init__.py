@@ -231,3 +231,24 @@ def jk_sample_pairs(ob, Ds, pairs, nthreads: int | None = None):
            nthreads if nthreads is not None else nthreads_default(),
            sel.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
     return J, K, int(nq)
+
+
+def jk_blocks(ob, Ds, pa, pb, nthreads: int | None = None):
+    """Whole J and K blocks of shell pairs (pa[i], pb[i]) from their
+    definitions, for a list of real densities: returns lists (one entry per
+    pair) of (J, K) arrays of shape (len(Ds), n_a, n_b)."""
+    Ds = [np.ascontiguousarray(D, dtype=np.float64) for D in Ds]
+    D = np.ascontiguousarray(np.stack(Ds))
+    pa = np.ascontiguousarray(pa, dtype=np.int32)
+    pb = np.ascontiguousarray(pb, dtype=np.int32)
+    npairs = int(pa.shape[0])
+    Jo = np.zeros((len(Ds), npairs, 36))
+    Ko = np.zeros((len(Ds), npairs, 36))
+    lib().or_jk_blocks(*ob.args(), len(Ds), _d(D), npairs, _i(pa), _i(pb), _d(Jo), _d(Ko),
+                       nthreads if nthreads is not None else nthreads_default())
+    nc = [(int(l) + 1) * (int(l) + 2) // 2 for l in ob.L]
+    out = []
+    for p in range(npairs):
+        na, nb = nc[pa[p]], nc[pb[p]]
+        out.append((Jo[:, p, :na * nb].reshape(len(Ds), na, nb), Ko[:, p, :na * nb].reshape(len(Ds), na, nb)))
+    return out

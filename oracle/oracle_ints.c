@@ -645,6 +645,75 @@ void or_jk_elements(int nsh, const double *ctr, const int *L, const int *np,
     basis_free(&B);
 }
 
+/* Whole shell-pair blocks straight from the definition, for sampling large
+ * cases: for each requested shell pair (a, b) and every (c, d),
+ *   J_{mn} += sum_{ls} (mn|ls) D_ls   (m in a, n in b; l in c, s in d),
+ *   K_{mn} += sum_{ls} (ml|sn) D_ls,
+ * nd densities.  Output Jo/Ko[(q * np + p) * 36 + m * nb + n]. */
+void or_jk_blocks(int nsh, const double *ctr, const int *L, const int *np,
+                  const int *poff, const double *ex, const double *co, int nd,
+                  const double *D, int npairs, const int *pa, const int *pb,
+                  double *Jo, double *Ko, int nthreads)
+{
+    Basis B;
+    basis_init(&B, nsh, ctr, L, np, poff, ex, co);
+    long n = B.nbf;
+    memset(Jo, 0, sizeof(double) * nd * npairs * 36);
+    memset(Ko, 0, sizeof(double) * nd * npairs * 36);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+    for (int p = 0; p < npairs; ++p) {
+        const int a = pa[p], b = pb[p];
+        const int na = NCART[L[a]], nb = NCART[L[b]];
+#pragma omp parallel
+        {
+            double blk[1296];
+            double *jt = (double *)calloc(nd * 36, sizeof(double));
+            double *kt = (double *)calloc(nd * 36, sizeof(double));
+#pragma omp for schedule(dynamic, 1)
+            for (int c = 0; c < nsh; ++c)
+                for (int d = 0; d < nsh; ++d) {
+                    const int nc = NCART[L[c]], ndd = NCART[L[d]];
+                    eri_block(&B, a, b, c, d, blk);          /* (ab|cd) */
+                    for (int m = 0; m < na; ++m)
+                        for (int k2 = 0; k2 < nb; ++k2)
+                            for (int l = 0; l < nc; ++l)
+                                for (int s = 0; s < ndd; ++s) {
+                                    const int i = B.bfo[a] + m, j = B.bfo[b] + k2;
+                                    const int k = B.bfo[c] + l, ll = B.bfo[d] + s;
+                                    const double v = blk[((m * nb + k2) * nc + l) * ndd + s] * B.f[i] *
+                                                     B.f[j] * B.f[k] * B.f[ll];
+                                    for (int q = 0; q < nd; ++q)
+                                        jt[q * 36 + m * nb + k2] += v * D[(long)q * n * n + k * n + ll];
+                                }
+                    eri_block(&B, a, c, d, b, blk);          /* (ac|db) */
+                    for (int m = 0; m < na; ++m)
+                        for (int l = 0; l < nc; ++l)
+                            for (int s = 0; s < ndd; ++s)
+                                for (int k2 = 0; k2 < nb; ++k2) {
+                                    const int i = B.bfo[a] + m, j = B.bfo[b] + k2;
+                                    const int k = B.bfo[c] + l, ll = B.bfo[d] + s;
+                                    const double v = blk[((m * nc + l) * ndd + s) * nb + k2] * B.f[i] *
+                                                     B.f[k] * B.f[ll] * B.f[j];
+                                    for (int q = 0; q < nd; ++q)
+                                        kt[q * 36 + m * nb + k2] += v * D[(long)q * n * n + k * n + ll];
+                                }
+                }
+#pragma omp critical
+            {
+                for (int q = 0; q < nd; ++q)
+                    for (int e = 0; e < 36; ++e) {
+                        Jo[((long)q * npairs + p) * 36 + e] += jt[q * 36 + e];
+                        Ko[((long)q * npairs + p) * 36 + e] += kt[q * 36 + e];
+                    }
+            }
+            free(jt); free(kt);
+        }
+    }
+    basis_free(&B);
+}
+
 /* Per-function renormalisation factors (exposed for tests). */
 void or_norm_factors(int nsh, const double *ctr, const int *L, const int *np,
                      const int *poff, const double *ex, const double *co, double *f)
