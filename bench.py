@@ -37,8 +37,9 @@ import synth  # noqa: E402
 METRIC = "J+K Fock builds/s & ERI quartets/s; mixed vs FP64 GPU at |dE|<=1e-6 Eh"
 WORKLOAD = "rt16: 16-atom O6H10 cluster, 210 Cartesian s,p,d functions, complex-Hermitian P (29 occ)"
 # precision split of the headline build: the mixed_tol sweep of this
-# workload (--workload tolsweep) gives |dE| 2.8e-7 Eh at 3e-3 (target 1e-6)
-MIXED_TOL = 3e-3
+# workload (--workload tolsweep) gives |dE| 2.3e-7 Eh at 5e-3 (target 1e-6,
+# a 4x margin; 1e-2 leaves 8.3e-7, too close), checked again in every run
+MIXED_TOL = 5e-3
 # the RT-TDHF comparison keeps a tighter split: its mixed run never returns
 # to all-FP64 builds, and the dipole error grows with the split
 RT_MIXED_TOL = 1e-3
@@ -53,6 +54,8 @@ def workload():
 
 
 # the large single J/K build: 100-atom cluster, split FP32/FP64 precision
+# (the tighter 3e-3 split: its energy error against an all-FP64 build is not
+# measured in the benchmark run)
 LARGE_WORKLOAD = ("large100: 100-atom cluster (H with p 0.25, else C/N/O), 1930 Cartesian s,p,d functions, "
                   "real P of 200 random orthonormal orbitals, Schwarz 1e-12")
 LARGE_MIXED_TOL = 3e-3
@@ -379,7 +382,9 @@ def run_gpu(args):
 
     # ---- kernel variant per class (autotuner; set-up, not timed)
     if not args.no_autotune:
-        b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=False)
+        # --tuning-cache reuses the table an earlier run stored (profiling runs
+        # that must launch exactly the timed build's kernels)
+        b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=args.tuning_cache)
     for spec in args.variant:          # QC:FP32:VARIANT, after the autotuner
         q, p32, v = (int(x) for x in spec.split(":"))
         b.set_variant(q, p32, v)
@@ -601,6 +606,40 @@ def run_tol_sweep(args):
     return 0
 
 
+def run_cluster30(args):
+    """A 30-atom cluster of the large workload's composition (598 functions):
+    mixed builds with the large workload's split and Schwarz threshold and
+    the default kernel variants -- a case small enough to profile the class
+    kernels of the large build one launch at a time."""
+    torch, cq = _driver_setup()
+    if cq is None:
+        return 0
+    mol = synth.cluster(30, 3333, p_h=0.25)
+    b = cq.Basis(mol, synth.basis_spd(mol, 3340))
+    P = torch.as_tensor(synth.density(b.nbf, 60, 11), device="cuda")
+    stream = torch.cuda.current_stream()
+    kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=LARGE_MIXED_TOL, schwarz_tol=LARGE_SCHWARZ)
+    for _ in range(args.warmup):
+        b.fock_build(P, **kw)
+    tms = []
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for _ in range(max(1, args.steps)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, st = b.fock_build(P, stats=True, **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tms.append(e0.elapsed_time(e1))
+    b.close()
+    ms = statistics.median(tms)
+    _line(METRIC, 1e3 / ms, "builds/s", True, args, ms,
+          {"workload": f"cluster30: 30-atom cluster (large100 composition), {b.nbf} functions, real P (60 occ)",
+           "mixed_tol": LARGE_MIXED_TOL, "schwarz_tol": LARGE_SCHWARZ},
+          {"quartets_per_build": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"]}}, clk,
+          None)
+    return 0
+
+
 def run_scf(args):
     """RHF direct SCF on the 16-atom workload: time to the converged energy,
     all-FP64 against mixed precision with incremental builds."""
@@ -774,9 +813,11 @@ def main():
                     help="keep the default kernel variant per class (profiling runs)")
     ap.add_argument("--variant", action="append", default=[], metavar="QC:FP32:V",
                     help="set the kernel variant of one class and precision (after autotuning)")
-    ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch", "tolsweep"],
+    ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch", "tolsweep", "cluster30"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
                          "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")
+    ap.add_argument("--tuning-cache", action="store_true",
+                    help="reuse (or store) the autotuned variant table instead of re-tuning")
     ap.add_argument("--large-steps", type=int, default=1,
                     help="timed mixed builds of the 100-atom configuration after the headline (0: skip)")
     ap.add_argument("--large-warmup", type=int, default=0)
@@ -797,6 +838,8 @@ def main():
         return run_batch(args)
     if args.workload == "tolsweep":
         return run_tol_sweep(args)
+    if args.workload == "cluster30":
+        return run_cluster30(args)
     return run_gpu(args)
 
 

@@ -8,7 +8,7 @@ split against the GPU's all-FP64 build) are checked on the full matrices.
 
 Tolerances: 1e-10 max-abs for all-FP64 builds (the method's FP64 target);
 for mixed builds 5e-6 max-abs per element (FP32 quartets carry bounds
-below mixed_tol = 3e-3 and relative rounding ~1e-7; their errors add up over
+below mixed_tol = 3e-3 or 5e-3 and relative rounding ~1e-7; their errors add up over
 the quartets touching an element) and |dE| <= 1e-6 Eh against all-FP64.
 """
 import numpy as np
@@ -19,7 +19,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-MIXED_TOL = 3e-3
+MIXED_TOL = 5e-3      # the benchmark's split of the rt16 build
 TOL_MIXED_ELEM = 5e-6
 
 
@@ -91,7 +91,7 @@ def test_rt16_benchmark_configuration(cq, orc):
 
 def test_large100_mixed(cq, orc):
     """The 100-atom, 1930-function single build with the benchmark's
-    split (FP32 below 3e-3, Schwarz 1e-12): whole blocks of 16 shell pairs
+    split for it (FP32 below 3e-3, Schwarz 1e-12): whole blocks of 16 shell pairs
     against the oracle, and the symmetry of the full matrices."""
     import torch
     mol, bas = synth.workload_large100()
@@ -100,7 +100,7 @@ def test_large100_mixed(cq, orc):
     assert n == 1930
     Ph = synth.density(n, 200, 11)
     P = torch.as_tensor(Ph, device="cuda")
-    J, K, st = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, schwarz_tol=1e-12, stats=True)
+    J, K, st = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=3e-3, schwarz_tol=1e-12, stats=True)
     assert st["quartets_fp32"] > 100 * st["quartets_fp64"] > 0
     pairs = _pairs(b.nshell, 16, 4)
     ref = orc.jk_blocks(orc.OBasis(mol, bas), [Ph], [p[0] for p in pairs], [p[1] for p in pairs])
@@ -131,7 +131,7 @@ def test_ghf40_pauli_fp64_and_mixed(cq, orc):
     Pc = _pauli_split(synth.spinor_density(n, int(mol.Z.sum()), 12))
     P = torch.as_tensor(np.ascontiguousarray(Pc), device="cuda")
     J, K = b.fock_build(P, schwarz_tol=1e-12)
-    Jm, Km = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, schwarz_tol=1e-12)
+    Jm, Km = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=3e-3, schwarz_tol=1e-12)
     pairs = _pairs(b.nshell, 16, 5)
     Ds = [Pc[0].real] + [x for I in range(4) for x in (Pc[I].real, Pc[I].imag)]
     ref = orc.jk_blocks(orc.OBasis(mol, bas), Ds, [p[0] for p in pairs], [p[1] for p in pairs])
