@@ -7,7 +7,8 @@ a real-time TDHF step contracts.  One step = one J+K build (every class
 kernel, density preparation and finalisation), Schwarz threshold 1e-14.
 
 Headline `value`: mixed-precision builds/s (FP32 for quartets whose Schwarz x
-density bound is below mixed_tol, everything accumulated in FP64), with the
+density bound is below mixed_tol, double-float -- FP32 pairs -- up to
+fp64_tol, FP64 above; everything accumulated exactly), with the
 energy error against the all-FP64 GPU build checked in the same run
 (|dE| <= 1e-6 Eh).  The all-FP64 rate is reported beside it.  The same run
 then times the 100-atom, 1930-function single build (split FP32/FP64,
@@ -40,6 +41,10 @@ WORKLOAD = "rt16: 16-atom O6H10 cluster, 210 Cartesian s,p,d functions, complex-
 # workload (--workload tolsweep) gives |dE| 2.3e-7 Eh at 5e-3 (target 1e-6,
 # a 4x margin; 1e-2 leaves 8.3e-7, too close), checked again in every run
 MIXED_TOL = 5e-3
+# double-float tier of the mixed builds: quartets with mixed_tol <= bound <
+# FP64_TOL in pairs of FP32 values (~48 bits, on the FP32 pipes), bound >=
+# FP64_TOL in FP64 (the sweep: 171 -> 122 ms at 5e-3, |dE| unchanged)
+FP64_TOL = 0.1
 # the RT-TDHF comparison keeps a tighter split: its mixed run never returns
 # to all-FP64 builds, and the dipole error grows with the split
 RT_MIXED_TOL = 1e-3
@@ -85,7 +90,8 @@ def large_leg(steps: int, warmup: int, fp64_ref: bool):
     J = torch.empty((n, n), dtype=torch.float64, device="cuda")
     K = torch.empty((n, n), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=LARGE_MIXED_TOL, schwarz_tol=LARGE_SCHWARZ, J=J, K=K)
+    kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=LARGE_MIXED_TOL, fp64_tol=FP64_TOL, schwarz_tol=LARGE_SCHWARZ,
+              J=J, K=K)
     for _ in range(warmup):
         b.fock_build(P, **kw)
     torch.cuda.synchronize()
@@ -105,35 +111,34 @@ def large_leg(steps: int, warmup: int, fp64_ref: bool):
     cls = b.class_stats()
     b.profile(False)
     peak64, peak32 = cq.peak_fma(False), cq.peak_fma(True)
+    peaks = prec_peaks(peak64, peak32)
     dom = None
-    f64 = f32 = 0.0
+    tot = [0.0, 0.0, 0.0]
     for key, v in cls.items():
         X, Y = cq.QUARTET_CLASSES[v["qc"]]
         v["flops"] = fl.class_flops(X, Y, v["quartets"], v["prims"], 1)
-        if v["fp32"]:
-            f32 += v["flops"]
-        else:
-            f64 += v["flops"]
+        tot[v["prec"]] += v["flops"]
         if dom is None or v["ms"] > cls[dom]["ms"]:
             dom = key
+    f64, f32, fdf = tot
     dv = cls[dom]
-    dpeak = peak32 if dv["fp32"] else peak64
+    dpeak = peaks[dv["prec"]]
     ms = sum(tms) / len(tms)
     out = {"workload": LARGE_WORKLOAD, "nbf": n, "nshell": b.nshell, "basis_setup_s": setup_s,
-           "mixed_tol": LARGE_MIXED_TOL, "schwarz_tol": LARGE_SCHWARZ, "steps": steps, "warmup": warmup,
+           "mixed_tol": LARGE_MIXED_TOL, "fp64_tol": FP64_TOL, "schwarz_tol": LARGE_SCHWARZ, "steps": steps,
+           "warmup": warmup,
            "builds_per_s": 1e3 / ms, "ms_per_build": ms,
-           "quartets_per_s": (st["quartets_fp64"] + st["quartets_fp32"]) * 1e3 / ms,
-           "quartets_per_build": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"]},
-           "prim_quartets_per_build": {"fp64": st["prim_fp64"], "fp32": st["prim_fp32"]},
-           "gflops_per_build": {"fp64": f64 * 1e-9, "fp32": f32 * 1e-9},
-           "build_roofline": {"min_ms": (f64 / peak64 + f32 / peak32) * 1e3, "ms": ms,
-                              "frac": (f64 / peak64 + f32 / peak32) * 1e3 / ms},
+           "quartets_per_s": (st["quartets_fp64"] + st["quartets_fp32"] + st["quartets_df"]) * 1e3 / ms,
+           "quartets_per_build": {"fp64": st["quartets_fp64"], "df": st["quartets_df"], "fp32": st["quartets_fp32"]},
+           "prim_quartets_per_build": {"fp64": st["prim_fp64"], "df": st["prim_df"], "fp32": st["prim_fp32"]},
+           "gflops_per_build": {"fp64": f64 * 1e-9, "df": fdf * 1e-9, "fp32": f32 * 1e-9},
+           "build_roofline": {"min_ms": sum(f / pk for f, pk in zip(tot, peaks)) * 1e3, "ms": ms,
+                              "frac": sum(f / pk for f, pk in zip(tot, peaks)) * 1e3 / ms},
            "roofline": {"bound": "alu", "kernel": dom, "achieved": dv["flops"] / (dv["ms"] * 1e-3) * 1e-12,
                         "peak": dpeak * 1e-12, "unit": "TFLOP/s",
                         "frac": dv["flops"] / (dv["ms"] * 1e-3) / dpeak, "traffic": None},
            "class_roofline": {k: {"ms": round(v["ms"], 2), "quartets": v["quartets"], "prims": v["prims"],
-                                  "frac": round(v["flops"] / max(v["ms"], 1e-9) * 1e3
-                                                / (peak32 if v["fp32"] else peak64), 4)}
+                                  "frac": round(v["flops"] / max(v["ms"], 1e-9) * 1e3 / peaks[v["prec"]], 4)}
                               for k, v in sorted(cls.items(), key=lambda kv: -kv[1]["ms"])},
            "clocks": clk.summary(), "accuracy_vs_fp64_gpu": None}
     if fp64_ref:
@@ -327,8 +332,8 @@ def cpu_baseline(seconds: float, ref_frac: float):
 
 # ---------------------------------------------------------------- GPU arm
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic_jk_rt16.json")
-KERNEL_SOURCES = ("cq_common.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "cq_sym.cuh", "gen_eri.py",
-                  "gen_coop.py", "gen_sym.py")
+KERNEL_SOURCES = ("cq_common.cuh", "cq_df.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "cq_sym.cuh",
+                  "gen_eri.py", "gen_coop.py", "gen_sym.py")
 
 
 def kernel_sources_sha1():
@@ -354,6 +359,13 @@ def traffic_of(key, cls, variant):
         if e.get("variant") == variant:
             return e["bytes_per_quartet"] * cls["quartets"]
     return None
+
+
+def prec_peaks(peak64, peak32):
+    """Roofline peaks of the three precisions: the measured FP64 and FP32 FMA
+    peaks, and for double-float the FP32 peak x 2/30 -- one double-float FMA
+    (2 FLOPs) is 15 FP32 instructions in this implementation (cq_df.cuh)."""
+    return (peak64, peak32, peak32 * 2.0 / 30.0)
 
 
 def run_gpu(args):
@@ -384,22 +396,23 @@ def run_gpu(args):
     if not args.no_autotune:
         # --tuning-cache reuses the table an earlier run stored (profiling runs
         # that must launch exactly the timed build's kernels)
-        b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, cache=args.tuning_cache)
-    for spec in args.variant:          # QC:FP32:VARIANT, after the autotuner
-        q, p32, v = (int(x) for x in spec.split(":"))
-        b.set_variant(q, p32, v)
-    tuned = {"variant": [[b.get_variant(q, 0), b.get_variant(q, 1)] for q in range(21)]}
+        b.autotune(P, prec=prec, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL if prec != cq.CQ_PREC_FP64 else 0.0,
+                   cache=args.tuning_cache)
+    for spec in args.variant:          # QC:PREC:VARIANT, after the autotuner
+        q, pv, v = (int(x) for x in spec.split(":"))
+        b.set_variant(q, pv, v)
+    tuned = {"variant": [[b.get_variant(q, p) for p in range(3)] for q in range(21)]}
 
     # ---- accuracy of the timed mode against the all-FP64 build (same run)
     J64, K64 = b.fock_build(P)
-    Jm, Km = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL)
+    Jm, Km = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL)
     dF = 2 * (Jm - J64).to(torch.complex128) - (Km - K64)
     dE = float(abs(torch.sum(dF * P.T).real.item()))
     dJ = float((Jm - J64).abs().max().item())
     dK = float((Km - K64).abs().max().item())
 
     def build():
-        b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, J=J, K=K)
+        b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, J=J, K=K)
 
     for _ in range(args.warmup):
         build()
@@ -424,29 +437,28 @@ def run_gpu(args):
 
     # ---- per-class profile (one extra build, events around each class kernel)
     b.profile(True)
-    _, _, st = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, J=J, K=K, stats=True)
+    _, _, st = b.fock_build(P, prec=prec, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, J=J, K=K, stats=True)
     cls = b.class_stats()
     b.profile(False)
-    quartets = st["quartets_fp64"] + st["quartets_fp32"]
+    quartets = st["quartets_fp64"] + st["quartets_fp32"] + st["quartets_df"]
     nk = 2
-    tot_flops64 = tot_flops32 = 0.0
+    peak64 = cq.peak_fma(False)
+    peak32 = cq.peak_fma(True)
+    peaks = prec_peaks(peak64, peak32)
+    tot = [0.0, 0.0, 0.0]
     dom = None
     for key, v in cls.items():
         X, Y = cq.QUARTET_CLASSES[v["qc"]]
         f = fl.class_flops(X, Y, v["quartets"], v["prims"], nk)
         v["flops"] = f
-        if v["fp32"]:
-            tot_flops32 += f
-        else:
-            tot_flops64 += f
+        tot[v["prec"]] += f
         if dom is None or v["ms"] > cls[dom]["ms"]:
             dom = key
-    peak64 = cq.peak_fma(False)
-    peak32 = cq.peak_fma(True)
+    tot_flops64, tot_flops32, tot_flopsdf = tot
     dv = cls[dom]
-    dom_peak = peak32 if dv["fp32"] else peak64
+    dom_peak = peaks[dv["prec"]]
     achieved = dv["flops"] / (dv["ms"] * 1e-3)
-    traffic = traffic_of(dom, dv, b.get_variant(dv["qc"], dv["fp32"]))
+    traffic = traffic_of(dom, dv, b.get_variant(dv["qc"], dv["prec"]))
 
     # ---- FP64-only rate (reported beside the headline)
     fp64_rate = None
@@ -474,7 +486,7 @@ def run_gpu(args):
     e0.record(stream)
     for _ in range(nrep):
         Pd = Ph_pin.to("cuda", non_blocking=True)
-        Jd, Kd = b.fock_build(Pd, prec=prec, mixed_tol=MIXED_TOL)
+        Jd, Kd = b.fock_build(Pd, prec=prec, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL)
         Jh.copy_(Jd, non_blocking=True)
         Kh.copy_(Kd, non_blocking=True)
     e1.record(stream)
@@ -489,32 +501,32 @@ def run_gpu(args):
         out = {"metric": METRIC, "value": value, "unit": "builds/s", "n_gpus": ws,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-               "dtype": "f64+f32" if prec != cq.CQ_PREC_FP64 else "f64", "data": "synthetic",
+               "dtype": "f64+df+f32" if prec != cq.CQ_PREC_FP64 else "f64", "data": "synthetic",
                "config": {"workload": WORKLOAD, "nbf": n, "precision": args.prec, "mixed_tol": MIXED_TOL,
-                          "schwarz_tol": 1e-14, "l2": "flushed (256 MiB write) between timed steps",
-                          "parallelism": f"replicas x{ws}"},
+                          "fp64_tol": FP64_TOL, "schwarz_tol": 1e-14,
+                          "l2": "flushed (256 MiB write) between timed steps", "parallelism": f"replicas x{ws}"},
                "quartets_per_s": value * quartets,
-               "quartets_per_build": {"fp64": st["quartets_fp64"], "fp32": st["quartets_fp32"]},
-               "prim_quartets_per_build": {"fp64": st["prim_fp64"], "fp32": st["prim_fp32"]},
+               "quartets_per_build": {"fp64": st["quartets_fp64"], "df": st["quartets_df"],
+                                      "fp32": st["quartets_fp32"]},
+               "prim_quartets_per_build": {"fp64": st["prim_fp64"], "df": st["prim_df"], "fp32": st["prim_fp32"]},
                "fp64_builds_per_s": fp64_rate if fp64_rate is not None else value,
                "accuracy_vs_fp64_gpu": {"dE_Eh": dE, "max_dJ": dJ, "max_dK": dK},
-               "gflops_per_build": {"fp64": tot_flops64 * 1e-9, "fp32": tot_flops32 * 1e-9},
-               # whole build against the time its FLOPs need at the measured
-               # FP64 and FP32 peaks (class kernels run concurrently)
-               "build_roofline": {"min_ms": (tot_flops64 / peak64 + tot_flops32 / peak32) * 1e3,
+               "gflops_per_build": {"fp64": tot_flops64 * 1e-9, "df": tot_flopsdf * 1e-9, "fp32": tot_flops32 * 1e-9},
+               # whole build against the time its FLOPs need at the three
+               # precisions' peaks (class kernels run concurrently)
+               "build_roofline": {"min_ms": sum(f / pk for f, pk in zip(tot, peaks)) * 1e3,
                                   "ms": tot_ms / args.steps,
-                                  "frac": (tot_flops64 / peak64 + tot_flops32 / peak32) * 1e3
-                                          / (tot_ms / args.steps)},
+                                  "frac": sum(f / pk for f, pk in zip(tot, peaks)) * 1e3 / (tot_ms / args.steps)},
                "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved * 1e-12,
                             "peak": dom_peak * 1e-12, "unit": "TFLOP/s", "frac": achieved / dom_peak,
                             "traffic": traffic,
-                            "peak_source": "measured FMA-chain peak in this run (cq_peak_fma), "
-                                           f"fp64 {peak64 * 1e-12:.3f} / fp32 {peak32 * 1e-12:.2f} TFLOP/s"},
+                            "peak_source": "measured FMA-chain peaks in this run (cq_peak_fma), "
+                                           f"fp64 {peak64 * 1e-12:.3f} / fp32 {peak32 * 1e-12:.2f} TFLOP/s; "
+                                           f"double-float = fp32 x 2/30 = {peaks[2] * 1e-12:.2f} TFLOP/s"},
                "tuned_variants": tuned["variant"],
                "class_roofline": {k: {"ms": round(v["ms"], 3), "quartets": v["quartets"], "prims": v["prims"],
                                       "tflops": round(v["flops"] / max(v["ms"], 1e-9) * 1e-9, 4),
-                                      "frac": round(v["flops"] / max(v["ms"], 1e-9) * 1e3
-                                                    / (peak32 if v["fp32"] else peak64), 4)}
+                                      "frac": round(v["flops"] / max(v["ms"], 1e-9) * 1e3 / peaks[v["prec"]], 4)}
                                   for k, v in sorted(cls.items(), key=lambda kv: -kv[1]["ms"])},
                "class_ms": {k: round(v["ms"], 3) for k, v in sorted(cls.items(), key=lambda kv: -kv[1]["ms"])},
                "e2e": {"value": e2e, "unit": "builds/s", "h2d_bytes_per_step": n * n * 16,
@@ -567,7 +579,7 @@ def run_tol_sweep(args):
     mol, bas, Ph = workload()
     b = cq.Basis(mol, bas)
     P = torch.as_tensor(Ph, device="cuda")
-    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, cache=False)
     J64, K64 = b.fock_build(P)
     flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -590,14 +602,19 @@ def run_tol_sweep(args):
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         t64 = timed()
         for tol in [float(x) for x in args.tols.split(",")]:
-            Jm, Km, st = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=tol, stats=True)
-            dF = 2 * (Jm - J64).to(torch.complex128) - (Km - K64)
-            rows.append({"mixed_tol": tol,
-                         "fp32_share": st["quartets_fp32"] / max(1, st["quartets_fp32"] + st["quartets_fp64"]),
-                         "dE_Eh": float(abs(torch.sum(dF * P.T).real.item())),
-                         "max_dJ": float((Jm - J64).abs().max().item()),
-                         "max_dK": float((Km - K64).abs().max().item()),
-                         "ms": timed(prec=cq.CQ_PREC_MIXED, mixed_tol=tol)})
+            for dtol in [float(x) for x in args.df_tols.split(",")]:
+                if dtol and dtol <= tol:
+                    continue
+                kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=tol, fp64_tol=dtol)
+                Jm, Km, st = b.fock_build(P, stats=True, **kw)
+                dF = 2 * (Jm - J64).to(torch.complex128) - (Km - K64)
+                nq = max(1, st["quartets_fp32"] + st["quartets_fp64"] + st["quartets_df"])
+                rows.append({"mixed_tol": tol, "fp64_tol": dtol,
+                             "fp32_share": st["quartets_fp32"] / nq, "df_share": st["quartets_df"] / nq,
+                             "dE_Eh": float(abs(torch.sum(dF * P.T).real.item())),
+                             "max_dJ": float((Jm - J64).abs().max().item()),
+                             "max_dK": float((Km - K64).abs().max().item()),
+                             "ms": timed(**kw)})
     b.close()
     best = min((r for r in rows if r["dE_Eh"] <= 1e-6), key=lambda r: r["ms"], default=None)
     _line("J+K build time vs precision split (mixed_tol sweep)", best["ms"] if best else None, "ms", False, args,
@@ -744,7 +761,7 @@ def run_batch(args):
         Pw[m, :n, :n] = torch.as_tensor(synth.density(n, no(test)[m], m))
     bte.autotune(Pw, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
     for qc in range(21):
-        for p in (0, 1):
+        for p in range(3):
             btr.set_variant(qc, p, bte.get_variant(qc, p))
     # training data: converged FP64 solutions of the training molecules
     t0 = time.perf_counter()
@@ -811,8 +828,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant per class (profiling runs)")
-    ap.add_argument("--variant", action="append", default=[], metavar="QC:FP32:V",
-                    help="set the kernel variant of one class and precision (after autotuning)")
+    ap.add_argument("--variant", action="append", default=[], metavar="QC:PREC:V",
+                    help="set the kernel variant of one class and precision (0 FP64, 1 FP32, 2 double-float; after autotuning)")
     ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch", "tolsweep", "cluster30"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
                          "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")
@@ -827,6 +844,8 @@ def main():
     ap.add_argument("--nmol", type=int, default=512)
     ap.add_argument("--ntrain", type=int, default=512)
     ap.add_argument("--tols", default="1e-2,3e-3,1e-3,1e-4,1e-5,1e-6")
+    ap.add_argument("--df-tols", default="0",
+                    help="fp64_tol values of the sweep (0: no double-float tier)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

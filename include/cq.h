@@ -108,10 +108,12 @@ void cq_basis_destroy(cq_basis* b);
  * code the integral kernels use (the [00|00]^(m) factor of the Obara-Saika
  * recurrence, Sec. "Reference Wave Functions" direct integral evaluation):
  * fp32 = 0 in FP64; fp32 = 1 in FP32 with the argument rounded to FP32 and
- * FP64 evaluation below T = 1/32 (the first table interval).
+ * FP64 evaluation below T = 1/32 (the first table interval); fp32 = 2 in
+ * double-float (pairs of FP32 numbers, about 48 significant bits).
  *   T: device, n doubles.  F: device, n x (mmax + 1) doubles, row-major
  *   (FP32 results widened).  The table lives in the basis handle b.
- *   Returns CQ_ERR_INVALID_ARG for mmax outside 0..8, n < 0 or NULL arrays. */
+ *   Returns CQ_ERR_INVALID_ARG for mmax outside 0..8, fp32 outside 0..2,
+ *   n < 0 or NULL arrays. */
 int cq_boys(const cq_basis* b, int fp32, int mmax, int n, const double* T, double* F, void* stream);
 
 /* cq_schwarz: Schwarz factors Q_ab = sqrt(max_{m in a, n in b} |(mn|mn)|)
@@ -126,6 +128,10 @@ typedef struct {
     double mixed_tol;    /* CQ_PREC_MIXED: quartets with bound < mixed_tol in FP32 */
     int prec;            /* cq_prec */
     int want_J, want_K;  /* 0/1 */
+    double fp64_tol;     /* CQ_PREC_MIXED: quartets with mixed_tol <= bound < fp64_tol in
+                            double-float (pairs of FP32 values, ~48 bits, on the FP32
+                            pipes); bound >= fp64_tol in FP64.  0 (or <= mixed_tol): no
+                            double-float tier */
 } cq_fock_opts;
 
 typedef struct {
@@ -133,6 +139,7 @@ typedef struct {
     unsigned long long quartets_fp32;  /* ... in FP32 (mixed precision)             */
     unsigned long long prim_fp64, prim_fp32; /* primitive quartets                   */
     double ms;                          /* device time of the build (CUDA events)   */
+    unsigned long long quartets_df, prim_df;  /* ... in double-float (fp64_tol tier) */
 } cq_fock_stats;
 
 /* cq_fock_build: J and K of a density (Eq. 2c_fock; Pauli components per
@@ -193,7 +200,8 @@ size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell);
  * cq_fock_profile(b, 1) makes later builds record CUDA events around each
  * angular-momentum-class kernel.  cq_fock_class_stats returns, for the last
  * build, class qc (0..20, bra class X >= ket class Y, qc = X(X+1)/2 + Y with
- * pair classes ss,ps,pp,ds,dp,dd = 0..5) and precision (fp32 0/1): kernel
+ * pair classes ss,ps,pp,ds,dp,dd = 0..5) and precision (fp32: 0 FP64,
+ * 1 FP32, 2 double-float): kernel
  * time in ms (0 if profiling was off), contracted and primitive quartets
  * evaluated.  Synchronises the device. */
 int cq_fock_profile(cq_basis* b, int enable);
@@ -201,18 +209,26 @@ int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms,
                         unsigned long long* quartets, unsigned long long* prims);
 
 /* Kernel variant used for one angular-momentum class (qc as for
- * cq_fock_class_stats) and precision: 0 = lane-group kernel (lanes of a warp
- * split one quartet's primitive quartets, generated straight-line
- * recurrences), 1 = warp-cooperative kernel (one warp per quartet walking
- * generated recurrence tables through shared memory), 2 = axis-permutation
- * lane groups (classes of total angular momentum >= 4 with a d shell, and
- * (pp|pp); FP64 too except (dd|dp) and (dd|dd): 3 or 6 lanes per quartet
- * each run the vertical recurrence for a third or a sixth of the targets on
- * axis-permuted inputs; CQ_ERR_UNSUPPORTED elsewhere).  All give the same J/K to rounding; the choice only changes
- * speed (set by the autotuner). */
-int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant);
+ * cq_fock_class_stats) and precision (prec: 0 FP64, 1 FP32, 2 double-float):
+ *   0 = lane-group kernel (lanes of a warp split one quartet's primitive
+ *       quartets, generated straight-line recurrences); double-float only
+ *       for classes of total angular momentum <= 3;
+ *   1 = warp-cooperative kernel (one warp per quartet walking generated
+ *       recurrence tables through shared memory) over one task per
+ *       (class, bra pair), screening inside the kernel; FP64 and FP32 only;
+ *   2 = axis-permutation lane groups (classes of total angular momentum
+ *       >= 4 with a d shell, and (pp|pp); FP64 and double-float too except
+ *       (dd|dp) and (dd|dd)): 3 or 6 lanes per quartet each run the
+ *       vertical recurrence for a third or a sixth of the targets on
+ *       axis-permuted inputs;
+ *   3 = the warp-cooperative kernel over the build's screened quartet
+ *       list, each quartet's primitive quartets split over up to four warps.
+ * CQ_ERR_UNSUPPORTED where a class has no such kernel, CQ_ERR_INVALID_ARG
+ * for arguments out of range.  All give the same J/K to rounding; the
+ * choice only changes speed (set by the autotuner). */
+int cq_fock_set_variant(cq_basis* b, int qc, int prec, int variant);
 
-int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
+int cq_fock_get_variant(const cq_basis* b, int qc, int prec, int* variant);
 
 /* Memory bound of the quartet lists (no paper counterpart).  A basis
  * created while the capacity is C keeps one list of min(C, candidates)
@@ -228,17 +244,19 @@ int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant);
 int cq_set_list_capacity(long long entries);
 long long cq_get_list_capacity(void);
 
-/* Autotuner: times every kernel variant a class has (the cooperative one
- * for total angular momentum >= 4, the axis-permutation one where it
- * exists; lighter classes keep lane groups) on the given density
- * (device, layout as for cq_fock_build) with the given options (NULL:
- * mixed precision, mixed_tol 1e-3), keeps the fastest variant per class and
- * precision in the basis, then tries the runner-up variant of each of the
- * six costliest classes in turn and keeps it only if the median of three
- * complete (concurrent) builds gets more than 1 % faster.  Returns the
- * choice in table[2*qc + fp32] and the best isolated kernel time in
- * ms_out[2*qc + fp32] (host arrays of 42, either may be NULL).  Runs up to
- * 27 builds; allocates and frees two output buffers. */
+/* Autotuner: times every kernel variant a class has (the cooperative ones
+ * for total angular momentum >= 4 only) at every precision the options use
+ * (FP64; FP64 and FP32; or FP64, FP32 and double-float when fp64_tol >
+ * mixed_tol) on the given density (device, layout as for cq_fock_build)
+ * with the given options (NULL: mixed precision, mixed_tol 1e-3), keeps the
+ * fastest variant per class and precision in the basis, then tries the
+ * runner-up variant of each of the eight costliest (class, precision)
+ * kernels in turn and keeps it only if the median of three complete
+ * (concurrent) builds gets more than 1 % faster.  Returns the choice in
+ * table[3*qc + prec] and the best isolated kernel time in
+ * ms_out[3*qc + prec] (0 for precisions not used; host arrays of 63, either
+ * may be NULL).  Runs up to 35 builds; allocates and frees two output
+ * buffers. */
 int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts,
                 int* table, double* ms_out, void* stream);
 

@@ -27,13 +27,14 @@ class CQError(RuntimeError):
 
 class FockOpts(ctypes.Structure):
     _fields_ = [("schwarz_tol", ctypes.c_double), ("mixed_tol", ctypes.c_double),
-                ("prec", ctypes.c_int), ("want_J", ctypes.c_int), ("want_K", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("want_J", ctypes.c_int), ("want_K", ctypes.c_int),
+                ("fp64_tol", ctypes.c_double)]
 
 
 class FockStats(ctypes.Structure):
     _fields_ = [("quartets_fp64", ctypes.c_ulonglong), ("quartets_fp32", ctypes.c_ulonglong),
                 ("prim_fp64", ctypes.c_ulonglong), ("prim_fp32", ctypes.c_ulonglong),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("quartets_df", ctypes.c_ulonglong), ("prim_df", ctypes.c_ulonglong)]
 
 
 class SCFOpts(ctypes.Structure):
@@ -273,13 +274,14 @@ class Basis:
         check(lib().cq_schwarz(self.h, _ptr(Q), _stream_ptr(stream)), "cq_schwarz")
         return Q
 
-    def boys(self, T, mmax: int, fp32: bool = False, stream=None):
+    def boys(self, T, mmax: int, fp32=False, stream=None):
         """F_0..F_mmax(T) for a CUDA float64 tensor T, evaluated by the
-        integral kernels' device Boys function (FP64 or FP32)."""
+        integral kernels' device Boys function: fp32 = False / 0 in FP64,
+        True / 1 in FP32, 2 in double-float."""
         import torch
         T = T.contiguous()
         F = torch.empty((T.numel(), mmax + 1), dtype=torch.float64, device=T.device)
-        check(lib().cq_boys(self.h, int(bool(fp32)), int(mmax), int(T.numel()), _ptr(T), _ptr(F),
+        check(lib().cq_boys(self.h, int(fp32), int(mmax), int(T.numel()), _ptr(T), _ptr(F),
                             _stream_ptr(stream)), "cq_boys")
         return F
 
@@ -296,10 +298,12 @@ class Basis:
         return E
 
     def fock_build(self, P, kind=None, schwarz_tol=1e-14, mixed_tol=1e-5, prec=CQ_PREC_FP64,
-                   want_J=True, want_K=True, J=None, K=None, stats=False, stream=None):
+                   want_J=True, want_K=True, J=None, K=None, stats=False, stream=None, fp64_tol=0.0):
         """J, K of a density given as a torch CUDA tensor:
         float64 (n, n) real symmetric; complex128 (n, n) Hermitian;
-        complex128 (4, n, n) Pauli components P^0..P^3."""
+        complex128 (4, n, n) Pauli components P^0..P^3.  In mixed precision,
+        fp64_tol > mixed_tol adds the double-float tier for bounds in
+        [mixed_tol, fp64_tol)."""
         import torch
         n = self.ld
         if kind is None:
@@ -320,7 +324,7 @@ class Basis:
                 K = torch.empty(shape, dtype=torch.complex128, device=P.device)
             else:
                 K = torch.empty((4,) + shape, dtype=torch.complex128, device=P.device)
-        o = FockOpts(schwarz_tol, mixed_tol, prec, int(want_J), int(want_K))
+        o = FockOpts(schwarz_tol, mixed_tol, prec, int(want_J), int(want_K), fp64_tol)
         st = FockStats()
         check(lib().cq_fock_build(self.h, kind, _ptr(P), _ptr(J) if want_J else None,
                                   _ptr(K) if want_K else None, ctypes.byref(o),
@@ -328,7 +332,8 @@ class Basis:
               "cq_fock_build")
         if stats:
             return J, K, {"quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32,
-                          "prim_fp64": st.prim_fp64, "prim_fp32": st.prim_fp32, "ms": st.ms}
+                          "prim_fp64": st.prim_fp64, "prim_fp32": st.prim_fp32, "ms": st.ms,
+                          "quartets_df": st.quartets_df, "prim_df": st.prim_df}
         return J, K
 
     def profile(self, enable: bool = True):
@@ -338,14 +343,14 @@ class Basis:
         """Per-class (time ms, quartets, primitive quartets) of the last build."""
         out = {}
         for qc, (X, Y) in enumerate(QUARTET_CLASSES):
-            for p in (0, 1):
+            for p in (0, 1, 2):
                 ms = ctypes.c_double()
                 nq, npq = ctypes.c_ulonglong(), ctypes.c_ulonglong()
                 check(lib().cq_fock_class_stats(self.h, qc, p, ctypes.byref(ms), ctypes.byref(nq),
                                                 ctypes.byref(npq)), "cq_fock_class_stats")
                 if nq.value or ms.value:
-                    key = f"({PAIR_CLASSES[X]}|{PAIR_CLASSES[Y]})" + ("f32" if p else "f64")
-                    out[key] = {"qc": qc, "fp32": p, "ms": ms.value, "quartets": nq.value,
+                    key = f"({PAIR_CLASSES[X]}|{PAIR_CLASSES[Y]})" + ("f64", "f32", "df")[p]
+                    out[key] = {"qc": qc, "fp32": int(p == 1), "prec": p, "ms": ms.value, "quartets": nq.value,
                                 "prims": npq.value}
         return out
 
@@ -421,41 +426,46 @@ class Basis:
               "cq_dense_info")
         return m.value, d.value
 
-    def set_variant(self, qc, fp32, variant):
-        check(lib().cq_fock_set_variant(self.h, int(qc), int(fp32), int(variant)), "cq_fock_set_variant")
+    def set_variant(self, qc, prec, variant):
+        """Kernel variant of class qc at precision prec (0 FP64, 1 FP32, 2
+        double-float): 0 lane groups, 1 cooperative (task mode), 2 axis
+        permutation, 3 cooperative on the screened list."""
+        check(lib().cq_fock_set_variant(self.h, int(qc), int(prec), int(variant)), "cq_fock_set_variant")
 
-    def get_variant(self, qc, fp32):
+    def get_variant(self, qc, prec):
         v = ctypes.c_int()
-        check(lib().cq_fock_get_variant(self.h, int(qc), int(fp32), ctypes.byref(v)), "cq_fock_get_variant")
+        check(lib().cq_fock_get_variant(self.h, int(qc), int(prec), ctypes.byref(v)), "cq_fock_get_variant")
         return v.value
 
-    def autotune(self, P, prec=CQ_PREC_MIXED, mixed_tol=1e-3, schwarz_tol=1e-14, cache=True, stream=None):
-        """Pick the fastest kernel variant per class (see cq_autotune).  With
-        cache=True the choice is stored per GPU model in _build/tuning.json
-        and reused by later calls instead of re-timing."""
+    def autotune(self, P, prec=CQ_PREC_MIXED, mixed_tol=1e-3, schwarz_tol=1e-14, fp64_tol=0.0, cache=True,
+                 stream=None):
+        """Pick the fastest kernel variant per class and precision (see
+        cq_autotune) for builds with these options.  With cache=True the
+        choice is stored per GPU model and split in _build/tuning.json and
+        reused by later calls instead of re-timing."""
         import json
         import torch
-        key = torch.cuda.get_device_name()
+        key = f"{torch.cuda.get_device_name()} prec={prec} mixed_tol={mixed_tol:g} fp64_tol={fp64_tol:g}"
         path = os.path.join(_HERE, "_build", "tuning.json")
         if cache and os.path.exists(path):
             try:
                 tab = json.load(open(path)).get(key)
             except Exception:
                 tab = None
-            if tab:
-                for qc, (v64, v32) in enumerate(tab["variant"]):
-                    self.set_variant(qc, 0, v64)
-                    self.set_variant(qc, 1, v32)
+            if tab and all(len(row) == 3 for row in tab["variant"]):
+                for qc, row in enumerate(tab["variant"]):
+                    for p, v in enumerate(row):
+                        self.set_variant(qc, p, v)
                 return tab
         kind = (CQ_DENS_REAL_SYM if P.dtype == torch.float64 else
                 CQ_DENS_PAULI4 if P.dim() == 3 else CQ_DENS_COMPLEX_HERM)
-        o = FockOpts(schwarz_tol, mixed_tol, prec, 1, 1)
-        tab = (ctypes.c_int * 42)()
-        ms = (ctypes.c_double * 42)()
+        o = FockOpts(schwarz_tol, mixed_tol, prec, 1, 1, fp64_tol)
+        tab = (ctypes.c_int * 63)()
+        ms = (ctypes.c_double * 63)()
         check(lib().cq_autotune(self.h, kind, _ptr(P.contiguous()), ctypes.byref(o), tab, ms,
                                 _stream_ptr(stream)), "cq_autotune")
-        out = {"variant": [[tab[2 * q], tab[2 * q + 1]] for q in range(21)],
-               "best_ms": [[ms[2 * q], ms[2 * q + 1]] for q in range(21)]}
+        out = {"variant": [[tab[3 * q + p] for p in range(3)] for q in range(21)],
+               "best_ms": [[ms[3 * q + p] for p in range(3)] for q in range(21)]}
         if cache:
             data = {}
             if os.path.exists(path):

@@ -31,6 +31,10 @@ LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
          "2120": 2, "2111": 2, "2210": 2, "1111": 2}
 
 
+# classes without an axis-permutation kernel: their double-float tier runs
+# the lane-group kernel (one lane per quartet)
+LANE_DF = ("0000", "1000", "1010", "1100", "1110", "2000", "2010", "2100")
+
 # axis-permutation kernels: lanes per frame splitting the primitive quartets
 # (FP64 lists are the short, large-bound part of a mixed build)
 SYM_H_F32, SYM_H_F64 = 1, 2
@@ -78,14 +82,18 @@ def gen_sources():
                 "}",
                 '#include "cq_jk.cuh"',
                 "namespace cq {"]
-        for R, tag in (("double", "f64"), ("float", "f32")):
+        precs = [("double", "f64"), ("float", "f32")]
+        if cls in LANE_DF:
+            precs.append(("df", "df"))
+        for R, tag in precs:
             src = head + [
                 f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
                 "{",
                 f"    const long long warps = (a.qmax + {32 // G} - 1) / {32 // G};",
                 "    long long blocks = (warps * 32 + JK_THREADS - 1) / JK_THREADS;",
                 "    if (blocks == 0) return;",
-                "    if (blocks > jk_grid_cap()) blocks = jk_grid_cap();",
+                "    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();",
+                "    if (blocks > cap) blocks = cap;",
                 f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<(unsigned)blocks, JK_THREADS, 0, s>>>(a);",
                 "}"]
             if X == Y and tag == "f64":
@@ -104,12 +112,17 @@ def gen_sources():
         c = f"{X[0]}{X[1]}{Y[0]}{Y[1]}"
         d.append(f"void launch_jk_{c}_f64(const JKArgs&, cudaStream_t);")
         d.append(f"void launch_jk_{c}_f32(const JKArgs&, cudaStream_t);")
-        d.append(f"static void launch_jk_{c}(const JKArgs& a, int fp32, cudaStream_t s) "
-                 f"{{ if (fp32) launch_jk_{c}_f32(a, s); else launch_jk_{c}_f64(a, s); }}")
+        if c in LANE_DF:
+            d.append(f"void launch_jk_{c}_df(const JKArgs&, cudaStream_t);")
+        df_call = f"else if (prec == 2) launch_jk_{c}_df(a, s); " if c in LANE_DF else ""
+        d.append(f"static void launch_jk_{c}(const JKArgs& a, int prec, cudaStream_t s) "
+                 f"{{ if (prec == 1) launch_jk_{c}_f32(a, s); {df_call}else launch_jk_{c}_f64(a, s); }}")
     for X in PCS:
         d.append(f"void launch_schwarz_{X[0]}{X[1]}(const JKArgs&, int, int, float*, double*, cudaStream_t);")
     d.append("const LaunchJK JK_LAUNCH[NQC] = {" +
              ", ".join(f"launch_jk_{X[0]}{X[1]}{Y[0]}{Y[1]}" for X, Y in qclasses()) + "};")
+    d.append("const int LANE_DF[NQC] = {" +
+             ", ".join("1" if f"{X[0]}{X[1]}{Y[0]}{Y[1]}" in LANE_DF else "0" for X, Y in qclasses()) + "};")
     d.append("const LaunchSchwarz SCHWARZ_LAUNCH[NPC] = {" +
              ", ".join(f"launch_schwarz_{X[0]}{X[1]}" for X in PCS) + "};")
     d.append("}  // namespace cq")
@@ -152,13 +165,15 @@ def gen_sources():
             "    const long long warps = (a.qmax + NGRP - 1) / NGRP;",
             "    long long blocks = (warps + WARPS - 1) / WARPS;",
             "    if (blocks == 0) return;",
-            "    if (blocks > jk_grid_cap()) blocks = jk_grid_cap();",
+            "    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();",
+            "    if (blocks > cap) blocks = cap;",
             "    kern<<<(unsigned)blocks, SYM_THREADS, bytes, s>>>(a, qc, nslots);",
             "}",
             f"void launch_sym_{cls}(const JKArgs& a, int fp32, cudaStream_t s)",
             "{",
-            f"    if (fp32) launch_sym_{cls}_t<float, {SYM_H_F32}>(a, s);"]
+            f"    if (fp32 == 1) launch_sym_{cls}_t<float, {SYM_H_F32}>(a, s);"]
         if f64:
+            lines.append(f"    else if (fp32 == 2) launch_sym_{cls}_t<df, {SYM_H_F64}>(a, s);")
             lines.append(f"    else launch_sym_{cls}_t<double, {SYM_H_F64}>(a, s);")
         lines += ["}", "}  // namespace cq"]
         write(os.path.join(GEN, f"cls_{cls}_sym.cu"), lines)

@@ -16,10 +16,12 @@ const int PC_L[NPC][2] = {{0, 0}, {1, 0}, {1, 1}, {2, 0}, {2, 1}, {2, 2}};
 // kernel variant per class before tuning: in FP64 the warp-cooperative
 // kernel for the classes with the largest recurrences, (dp|dp) (dd|pp)
 // (dd|dp) (dd|dd); in FP32 the axis-permutation lane groups for every class
-// of total angular momentum 6 or more; lane groups elsewhere
-const int DEFAULT_VARIANT[NQC][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
-                                     {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0},
-                                     {1, 2}, {0, 0}, {0, 0}, {1, 2}, {0, 2}, {1, 2}, {1, 2}};
+// of total angular momentum 6 or more; in double-float the axis-permutation
+// kernel up to total angular momentum 5, the cooperative kernel on the
+// screened list above, lane groups for the light classes
+const int DEFAULT_VARIANT[NQC][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {0, 0, 2}, {0, 0, 0},
+                                     {0, 0, 0}, {0, 0, 2}, {0, 0, 2}, {0, 0, 0}, {0, 0, 2}, {0, 0, 2}, {0, 0, 2},
+                                     {1, 2, 3}, {0, 0, 2}, {0, 0, 2}, {1, 2, 3}, {0, 2, 3}, {1, 2, 3}, {1, 2, 3}};
 
 static thread_local std::string g_err;
 
@@ -58,6 +60,9 @@ __global__ void boys_table_kernel(double* tab, float* tabf)
     tab[k * BOYS_D_COLS + BOYS_D_EXP + 1] = 0.0;
     for (int m = 0; m < BOYS_F_EXP; ++m) tabf[k * BOYS_F_COLS + m] = (float)F[m];
     tabf[k * BOYS_F_COLS + BOYS_F_EXP] = (float)e;
+    df* tabx = reinterpret_cast<df*>(tabf + boys_x_offset());
+    for (int m = 0; m < 16; ++m) tabx[k * BOYS_X_COLS + m] = df(F[m]);
+    tabx[k * BOYS_X_COLS + BOYS_X_EXP] = df(e);
 }
 
 __device__ double dfact_odd(int n)  // (n)!! for odd n >= -1
@@ -111,7 +116,7 @@ __global__ void scale_kernel(int nsh, const int* L, const int* bfo, double* scal
 // Primitive-pair data, one thread per shell pair.
 __global__ void pair_prep_kernel(int npair, const PairHdr* pairs, const double* ctr, const int* np,
                                  const int* poff, const double* ex, const double* coef, PrimPair* out,
-                                 PrimPairF* outf)
+                                 PrimPairF* outf, PrimPairX* outx)
 {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= npair) return;
@@ -140,6 +145,10 @@ __global__ void pair_prep_kernel(int npair, const PairHdr* pairs, const double* 
             for (int x = 0; x < 3; ++x) { f.P[x] = (float)o.P[x]; f.PA[x] = (float)o.PA[x]; }
             f.pad[0] = f.pad[1] = f.pad[2] = 0.f;
             outf[q] = f;
+            PrimPairX x;
+            x.zeta = df(o.zeta); x.oo2z = df(o.oo2z); x.K = df(o.K);
+            for (int c = 0; c < 3; ++c) { x.P[c] = df(o.P[c]); x.PA[c] = df(o.PA[c]); x.pad[c] = df(0.0); }
+            outx[q] = x;
         }
 }
 
@@ -153,7 +162,7 @@ static void free_basis(cq_basis* b)
 {
     if (!b) return;
     dense_free(b);
-    void* ptrs[] = {b->d_pass_qoff, b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_tasks,
+    void* ptrs[] = {b->d_pass_qoff, b->d_boys, b->d_boysf, b->d_pairs, b->d_prims, b->d_primsf, b->d_primsx, b->d_tasks,
                     b->d_Qf, b->d_Qd, b->d_scale, b->d_ctr, b->d_L, b->d_nprim, b->d_poff,
                     b->d_bfo, b->d_exps, b->d_coef, b->d_axyz, b->d_Z, b->d_Dp, b->d_Jp,
                     b->d_Kp, b->d_Dmax, b->d_cnt, b->d_coop_tasks, b->d_qlist, b->d_qcount,
@@ -164,11 +173,11 @@ static void free_basis(cq_basis* b)
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 3; ++p)
             for (int e = 0; e < 2; ++e)
                 if (b->pev[q][p][e]) cudaEventDestroy(b->pev[q][p][e]);
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p)
+        for (int p = 0; p < 3; ++p)
             for (cudaEvent_t ev : b->pev_pass[q][p]) cudaEventDestroy(ev);
     for (int k = 0; k < cq_basis::NSIDE; ++k) {
         if (b->side[k]) cudaStreamDestroy(b->side[k]);
@@ -197,8 +206,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
     b->atom_mol.assign(natom, 0);
     if (atom_mol) b->atom_mol.assign(atom_mol, atom_mol + natom);
     for (int q = 0; q < NQC; ++q) {
-        b->variant[q][0] = DEFAULT_VARIANT[q][0];
-        b->variant[q][1] = DEFAULT_VARIANT[q][1];
+        for (int p = 0; p < 3; ++p) b->variant[q][p] = DEFAULT_VARIANT[q][p];
     }
     b->natom = natom;
     b->nsh = nshell;
@@ -370,9 +378,9 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
         std::vector<long long> pq = {0, b->list_cap};
         if ((rc = upload(&b->d_pass_qoff, pq))) return rc;
     }
-    if ((rc = dalloc(&b->d_qcount, 2 * NQC))) return rc;
-    if ((rc = dalloc(&b->d_tcount, 2 * tasks.size()))) return rc;
-    if ((rc = dalloc(&b->d_toff, 2 * tasks.size()))) return rc;
+    if ((rc = dalloc(&b->d_qcount, 3 * NQC))) return rc;
+    if ((rc = dalloc(&b->d_tcount, 3 * tasks.size()))) return rc;
+    if ((rc = dalloc(&b->d_toff, 3 * tasks.size()))) return rc;
     if ((rc = upload(&b->d_axyz, axyz))) return rc;
     if ((rc = upload(&b->d_mol_n, b->mol_n))) return rc;
     if ((rc = upload(&b->d_mol_bfo, b->mol_bfo))) return rc;
@@ -384,11 +392,12 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
     if ((rc = dalloc(&b->d_scale, nbf))) return rc;
     if ((rc = dalloc(&b->d_prims, b->nprim_pairs))) return rc;
     if ((rc = dalloc(&b->d_primsf, b->nprim_pairs))) return rc;
+    if ((rc = dalloc(&b->d_primsx, b->nprim_pairs))) return rc;
     if ((rc = dalloc(&b->d_boys, (size_t)BOYS_NT * BOYS_D_COLS))) return rc;
-    if ((rc = dalloc(&b->d_boysf, (size_t)BOYS_NT * BOYS_F_COLS))) return rc;
+    if ((rc = dalloc(&b->d_boysf, boys_x_offset() + (size_t)2 * BOYS_NT * BOYS_X_COLS))) return rc;
     if ((rc = dalloc(&b->d_Qf, b->npair))) return rc;
     if ((rc = dalloc(&b->d_Qd, b->npair))) return rc;
-    if ((rc = dalloc(&b->d_cnt, 4 + 6 * NQC))) return rc;
+    if ((rc = dalloc(&b->d_cnt, CNT_WORDS))) return rc;
     {
         std::vector<double> coefs_raw(coefs, coefs + np);
         double* d_raw = nullptr;
@@ -403,7 +412,7 @@ static int create_impl(int natom, const double* xyz, const int* Z, const int* at
     boys_table_kernel<<<(BOYS_NT + 127) / 128, 128>>>(b->d_boys, b->d_boysf);
     pair_prep_kernel<<<(b->npair + 127) / 128, 128>>>(b->npair, b->d_pairs, b->d_ctr, b->d_nprim,
                                                       b->d_poff, b->d_exps, b->d_coef, b->d_prims,
-                                                      b->d_primsf);
+                                                      b->d_primsf, b->d_primsx);
     CQ_CUDA(cudaGetLastError());
     CQ_CUDA(cudaEventCreate(&b->ev0));
     CQ_CUDA(cudaEventCreate(&b->ev1));
@@ -611,14 +620,15 @@ __global__ void boys_eval_kernel(int mmax, int n, const double* __restrict__ T, 
 
 extern "C" int cq_boys(const cq_basis* b, int fp32, int mmax, int n, const double* T, double* F, void* stream)
 {
-    if (!b || (n > 0 && (!T || !F)) || mmax < 0 || mmax > LTOT_MAX || n < 0 || fp32 < 0 || fp32 > 1) {
+    if (!b || (n > 0 && (!T || !F)) || mmax < 0 || mmax > LTOT_MAX || n < 0 || fp32 < 0 || fp32 > 2) {
         set_error("cq_boys: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
     if (n == 0) return CQ_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int blocks = (n + 127) / 128;
-    if (fp32) boys_eval_kernel<float><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
+    if (fp32 == 2) boys_eval_kernel<df><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
+    else if (fp32) boys_eval_kernel<float><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
     else boys_eval_kernel<double><<<blocks, 128, 0, s>>>(mmax, n, T, b->d_boys, b->d_boysf, F);
     CQ_CUDA(cudaGetLastError());
     return CQ_OK;

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cq_df.cuh"
+
 namespace cq {
 
 constexpr int LMAX = 2;
@@ -22,6 +24,7 @@ struct __align__(16) PrimPairT {
 };
 using PrimPair = PrimPairT<double>;
 using PrimPairF = PrimPairT<float>;
+using PrimPairX = PrimPairT<df>;     // double-float shadow
 
 // Contracted shell pair header.
 struct PairHdr {
@@ -63,6 +66,12 @@ constexpr int BOYS_D_TAYLOR = 8;         // terms j = 0..7 (FP64)
 constexpr int BOYS_F_COLS = 14;          // m = 0..12, col 13 = e^{-T_k}
 constexpr int BOYS_F_EXP = 13;
 constexpr int BOYS_F_TAYLOR = 5;         // terms j = 0..4 (FP32)
+// double-float table, stored right after the FP32 one in the same array:
+// m = 0..15, col 16 = e^{-T_k}, each as a (hi, lo) pair
+constexpr int BOYS_X_COLS = 17;
+constexpr int BOYS_X_EXP = 16;
+constexpr int BOYS_X_TAYLOR = 8;         // terms j = 0..7
+__host__ __device__ constexpr size_t boys_x_offset() { return (size_t)BOYS_NT * BOYS_F_COLS; }   // in floats
 
 template <int L>
 __device__ __forceinline__ void boys(double T, double* F, const double* __restrict__ tab)
@@ -205,6 +214,48 @@ __device__ __forceinline__ void boys_q(float T, float* F, const double* __restri
         for (int m = 0; m <= L; ++m) F[m] = (float)Fd[m];
     } else {
         boys<L>(T, F, tabf);
+    }
+}
+
+// Double-float: the same tabulated Taylor expansion (8 terms, |delta| <=
+// 1/32) and downward recursion in double-float arithmetic from the
+// double-float table; for T >= 40 the asymptotic form with a double-float
+// reciprocal and square root, and e^{-T} in FP32 (below 4.3e-18 there, its
+// FP32 rounding is far below the double-float precision of the result).
+template <int L>
+__device__ __forceinline__ void boys_q(df T, df* F, const double* __restrict__, const float* __restrict__ tabf)
+{
+    const df* __restrict__ tab = reinterpret_cast<const df*>(tabf + boys_x_offset());
+    if (T.hi < (float)BOYS_TMAX) {
+        const int k = __float2int_rn(T.hi * 16.0f);
+        const df d(T.hi - 0.0625f * (float)k, T.lo);      // T - T_k (the FP32 difference is exact)
+        const df md = -d;
+        const df* row = tab + k * BOYS_X_COLS;
+        df c[BOYS_X_TAYLOR];
+#pragma unroll
+        for (int j = 1; j < BOYS_X_TAYLOR; ++j) c[j] = md * df(1.0 / j);
+        df f = row[L + BOYS_X_TAYLOR - 1];
+#pragma unroll
+        for (int j = BOYS_X_TAYLOR - 1; j >= 1; --j) f = fma(f, c[j], row[L + j - 1]);
+        F[L] = f;
+        if (L > 0) {
+            df e(1.f, 0.f);
+#pragma unroll
+            for (int j = BOYS_X_TAYLOR - 1; j >= 1; --j) e = fma(e, c[j], df(1.f, 0.f));
+            e = e * row[BOYS_X_EXP];
+            const df t2 = T + T;
+#pragma unroll
+            for (int m = L - 1; m >= 0; --m) F[m] = fma(t2, F[m + 1], e) * df(1.0 / (2 * m + 1));
+        }
+    } else {
+        const df it = recip(T);
+        F[0] = sqrt_df(it) * df(0.88622692545275801365);   // sqrt(pi)/2
+        if (L > 0) {
+            const df e(__expf(-T.hi), 0.f);
+            const df o2t = it * df(0.5f, 0.f);
+#pragma unroll
+            for (int m = 0; m < L; ++m) F[m + 1] = (F[m] * df(2 * m + 1) - e) * o2t;
+        }
     }
 }
 

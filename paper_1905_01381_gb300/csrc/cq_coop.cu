@@ -17,21 +17,26 @@ static void launch_coop_t(const JKArgs& a, int qc, cudaStream_t s)
         cudaFuncSetAttribute(jk_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_done = 1;
     }
-    const int blocks = (a.ntasks + COOP_WARPS - 1) / COOP_WARPS;
+    const long long tasks = (long long)a.ntasks * (a.coop_list ? COOP_LIST_SPLIT : 1);
+    long long blocks = (tasks + COOP_WARPS - 1) / COOP_WARPS;
     if (blocks == 0) return;
-    jk_coop_kernel<R><<<blocks, COOP_THREADS, bytes, s>>>(a, qc, nslots);
+    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();
+    if (a.coop_list && blocks > cap) blocks = cap;   // warps stride over the list
+    jk_coop_kernel<R><<<(unsigned)blocks, COOP_THREADS, bytes, s>>>(a, qc, nslots);
 }
 
-void launch_coop(const JKArgs& a, int qc, int fp32, cudaStream_t s)
+// prec: 0 FP64, 1 FP32, 2 double-float
+void launch_coop(const JKArgs& a, int qc, int prec, cudaStream_t s)
 {
-    if (fp32) launch_coop_t<float>(a, qc, s);
+    if (prec == 1) launch_coop_t<float>(a, qc, s);
+    else if (prec == 2) launch_coop_t<df>(a, qc, s);
     else launch_coop_t<double>(a, qc, s);
 }
 
-size_t coop_smem_bytes(int qc, int fp32)
+size_t coop_smem_bytes(int qc, int prec)
 {
     const int nslots = COOP_SIZES[qc].nslots;
-    return (size_t)COOP_WARPS * (fp32 ? coop_warp_bytes<float>(nslots) : coop_warp_bytes<double>(nslots));
+    return (size_t)COOP_WARPS * (prec == 1 ? coop_warp_bytes<float>(nslots) : coop_warp_bytes<double>(nslots));
 }
 
 }  // namespace cq

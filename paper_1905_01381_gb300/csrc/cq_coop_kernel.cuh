@@ -149,7 +149,118 @@ __device__ __forceinline__ void coop_hrr_digest(const CoopClass& C, R* __restric
 }
 
 template <typename R>
-struct CoopMinBlocks { static constexpr int v = sizeof(R) == 4 ? 8 : 6; };
+struct CoopMinBlocks { static constexpr int v = sizeof(R) == 4 ? 8 : 6; };   // df: 8 bytes, as FP64
+
+// Screening of a task of the candidate-task mode (list mode quartets are
+// already screened): a molecule in all-FP64 mode sends every survivor to the
+// FP64 half; a skipped molecule has none.
+__device__ __forceinline__ bool coop_selected(const JKArgs& a, const PairHdr& B, const PairHdr& K, int ib, int j)
+{
+    const float* Dm = a.Dmax;
+    const int ns = a.nsh;
+    const float* Ds = Dm + B.smbase;
+    float m = fmaxf(__ldg(Ds + B.sa * ns + B.sb), __ldg(Ds + K.sa * ns + K.sb));
+    m = fmaxf(m, fmaxf(__ldg(Ds + B.sa * ns + K.sa), __ldg(Ds + B.sa * ns + K.sb)));
+    m = fmaxf(m, fmaxf(__ldg(Ds + B.sb * ns + K.sa), __ldg(Ds + B.sb * ns + K.sb)));
+    const float bound = __ldg(a.Q + ib) * __ldg(a.Q + j) * m;
+    const int mode = a.mol_mode ? __ldg(a.mol_mode + B.smbase / a.lds2) : 1;
+    const float tm = (mode & 1) ? a.tau_mixed : 0.f;
+    bool sel = bound >= a.tau && !(mode & 2);
+    if (a.prec_sel == 1) sel = sel && bound >= tm;
+    else if (a.prec_sel == 2) sel = sel && bound < tm;
+    return sel;
+}
+
+// One task: primitive quartets [p0, p1) of quartet (ib, j), their vertical
+// recurrences, the contraction, HRR and digestion.  HRR and digestion are
+// linear, so a chunk of primitive quartets is digested on its own and the
+// J'/K' adds of all chunks sum to the quartet's.
+template <typename R>
+__device__ __forceinline__ void coop_task(const JKArgs& a, const CoopClass& C, int ib, int j, int p0, int p1,
+                                          const PairHdr& B, const PairHdr& K, R* __restrict__ coef,
+                                          R* __restrict__ Sb, R* __restrict__ V, R* __restrict__ Db,
+                                          R* __restrict__ hc, int lane, unsigned long long& nq,
+                                          unsigned long long& np)
+{
+    // ---- primitive quartets: coefficients, VRR, accumulation
+    R acc[COOP_MAXACC];
+#pragma unroll
+    for (int k = 0; k < COOP_MAXACC; ++k) acc[k] = R(0);
+    const int nkp = K.nprim;
+    for (int base = p0; base < p1; base += 32) {
+        const int cnt = min(32, p1 - base);
+        if (lane < cnt) {
+            const int pq = base + lane;
+            const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
+            PrimPairT<R> bp, kp;
+            load_prim<R>(a, B.poff + ip, bp);
+            load_prim<R>(a, K.poff + jp, kp);
+            const R s = bp.zeta + kp.zeta;
+            const R rs = rsqrt_r(s);
+            const R is = rs * rs;
+            const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
+            const R roz = kp.zeta * is, roe = bp.zeta * is;
+            const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
+            R F[LTOT_MAX + 1];
+            boys_rt_any<R>(C.L, T, F, a.boys_d, a.boys_f);
+            const R pref = bp.K * kp.K * rs;
+            R* cf = coef + lane * COOP_NCOEF;
+            cf[0] = bp.PA[0]; cf[1] = bp.PA[1]; cf[2] = bp.PA[2];
+            cf[3] = kp.PA[0]; cf[4] = kp.PA[1]; cf[5] = kp.PA[2];
+            cf[6] = -roz * PQx; cf[7] = -roz * PQy; cf[8] = -roz * PQz;
+            cf[9] = roe * PQx; cf[10] = roe * PQy; cf[11] = roe * PQz;
+            cf[12] = roz; cf[13] = roe;
+            const R o2ze = R(0.5) * is;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cf[14 + k] = R(k + 1) * bp.oo2z;
+                cf[18 + k] = R(k + 1) * kp.oo2z;
+                cf[22 + k] = R(k + 1) * o2ze;
+            }
+            R* sb = Sb + lane * (LTOT_MAX + 1);
+            for (int m = 0; m <= C.L; ++m) sb[m] = pref * F[m];
+        }
+        __syncwarp();
+        for (int q = 0; q < cnt; ++q) {
+            if (lane <= C.L) V[lane] = Sb[q * (LTOT_MAX + 1) + lane];
+            __syncwarp();
+            const R* cf = coef + q * COOP_NCOEF;
+            int4 Gn = __ldg(C.vgrp);
+            for (int g = 0; g < C.nvg;) {
+                const int4 G = Gn;
+                // the next group of the same level is independent: evaluate both
+                const bool pair = !G.w && g + 1 < C.nvg;
+                const int4 G2 = pair ? __ldg(C.vgrp + g + 1) : G;
+                const int gn = g + (pair ? 2 : 1);
+                if (gn < C.nvg) Gn = __ldg(C.vgrp + gn);
+                R v1 = R(0), v2 = R(0);
+                int o1 = -1, o2 = -1;
+                if (lane < G.y) o1 = coop_node<R>(G.x, __ldg(C.vdesc + G.z + lane), cf, V, v1);
+                if (pair && lane < G2.y) o2 = coop_node<R>(G2.x, __ldg(C.vdesc + G2.z + lane), cf, V, v2);
+                if (o1 >= 0) V[o1] = v1;
+                if (o2 >= 0) V[o2] = v2;
+                if ((pair ? G2.w : G.w)) __syncwarp();
+                g = gn;
+            }
+#pragma unroll
+            for (int k = 0; k < COOP_MAXACC; ++k) {
+                const int tt = lane + 32 * k;
+                if (tt < C.nacc) acc[k] += V[__ldg(C.tgt + tt)];
+            }
+            __syncwarp();
+        }
+        if (lane == 0) { nq += (base == 0); np += cnt; }
+    }
+
+    // ---- horizontal recurrence on the contracted block
+#pragma unroll
+    for (int k = 0; k < COOP_MAXACC; ++k) {
+        const int tt = lane + 32 * k;
+        if (tt < C.nacc) V[C.N + tt] = acc[k];
+    }
+    coop_hrr_digest<R>(C, V, Db, hc, B, K, ib, j, a, lane);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
 {
@@ -162,121 +273,39 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
     R* V = Sb + 32 * (LTOT_MAX + 1);                       // [nslots]
     R* Db = V + nslots_max;                                // 6 density blocks of <= 36
     R* hc = Db + 6 * 36;                                   // AB, CD
-
-    const int w = blockIdx.x * COOP_WARPS + wib;
-    if (w >= a.ntasks) return;
-    // task: bra pair, ket pair, primitive-quartet range [p0, p1).  HRR and
-    // digestion are linear, so a chunk of primitive quartets is digested on
-    // its own and the J'/K' adds of all chunks sum to the quartet's.  In
-    // list mode the task is a screened quartet of the list, all primitives.
-    int4 t;
-    if (a.coop_list) {
-        if (w >= (int)*a.qcount) return;
-        const int2 e = a.qlist[(long long)w * a.qdir];
-        t = make_int4(e.x, e.y, 0, 0);
-    } else {
-        t = a.tasks[w];
-    }
-    const int ib = t.x, j = t.y, p0 = t.z;
-    const PairHdr B = a.pairs[ib];
-    const PairHdr K = a.pairs[j];
-    const int p1 = a.coop_list ? B.nprim * K.nprim : t.w;
-    if (!a.coop_list) {
-        const float* Dm = a.Dmax;
-        const int ns = a.nsh;
-        const float* Ds = Dm + B.smbase;
-        float m = fmaxf(__ldg(Ds + B.sa * ns + B.sb), __ldg(Ds + K.sa * ns + K.sb));
-        m = fmaxf(m, fmaxf(__ldg(Ds + B.sa * ns + K.sa), __ldg(Ds + B.sa * ns + K.sb)));
-        m = fmaxf(m, fmaxf(__ldg(Ds + B.sb * ns + K.sa), __ldg(Ds + B.sb * ns + K.sb)));
-        const float bound = __ldg(a.Q + ib) * __ldg(a.Q + j) * m;
-        // a molecule in all-FP64 mode sends every survivor to the FP64 half;
-        // a skipped molecule has none
-        const int mode = a.mol_mode ? __ldg(a.mol_mode + B.smbase / a.lds2) : 1;
-        const float tm = (mode & 1) ? a.tau_mixed : 0.f;
-        bool sel = bound >= a.tau && !(mode & 2);
-        if (a.prec_sel == 1) sel = sel && bound >= tm;
-        else if (a.prec_sel == 2) sel = sel && bound < tm;
-        if (!sel) return;
-    }
     unsigned long long nq = 0, np = 0;
-    {
-        // ---- primitive quartets: coefficients, VRR, accumulation
-        R acc[COOP_MAXACC];
-#pragma unroll
-        for (int k = 0; k < COOP_MAXACC; ++k) acc[k] = R(0);
-        const int nkp = K.nprim;
-        for (int base = p0; base < p1; base += 32) {
-            const int cnt = min(32, p1 - base);
-            if (lane < cnt) {
-                const int pq = base + lane;
-                const int ip = pq / nkp, jp = pq - (pq / nkp) * nkp;
-                PrimPairT<R> bp, kp;
-                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
-                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
-                const R s = bp.zeta + kp.zeta;
-                const R rs = rsqrt_r(s);
-                const R is = rs * rs;
-                const R PQx = bp.P[0] - kp.P[0], PQy = bp.P[1] - kp.P[1], PQz = bp.P[2] - kp.P[2];
-                const R roz = kp.zeta * is, roe = bp.zeta * is;
-                const R T = roz * bp.zeta * (PQx * PQx + PQy * PQy + PQz * PQz);
-                R F[LTOT_MAX + 1];
-                boys_rt_any<R>(C.L, T, F, a.boys_d, a.boys_f);
-                const R pref = bp.K * kp.K * rs;
-                R* cf = coef + lane * COOP_NCOEF;
-                cf[0] = bp.PA[0]; cf[1] = bp.PA[1]; cf[2] = bp.PA[2];
-                cf[3] = kp.PA[0]; cf[4] = kp.PA[1]; cf[5] = kp.PA[2];
-                cf[6] = -roz * PQx; cf[7] = -roz * PQy; cf[8] = -roz * PQz;
-                cf[9] = roe * PQx; cf[10] = roe * PQy; cf[11] = roe * PQz;
-                cf[12] = roz; cf[13] = roe;
-                const R o2ze = R(0.5) * is;
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    cf[14 + k] = R(k + 1) * bp.oo2z;
-                    cf[18 + k] = R(k + 1) * kp.oo2z;
-                    cf[22 + k] = R(k + 1) * o2ze;
-                }
-                R* sb = Sb + lane * (LTOT_MAX + 1);
-                for (int m = 0; m <= C.L; ++m) sb[m] = pref * F[m];
-            }
+    if (a.coop_list) {
+        // list mode: the warps stride over the screened quartets of the list,
+        // each split into up to COOP_LIST_SPLIT equal ranges of its primitive
+        // quartets (at least 32 each), one range per warp task, so that a
+        // short list of deep quartets still spreads over the GPU (grid sized
+        // for the list capacity, capped; short lists leave the extra warps
+        // idle at once)
+        const long long cnt = (long long)*a.qcount * COOP_LIST_SPLIT;
+        const long long nw = (long long)gridDim.x * COOP_WARPS;
+        for (long long v = (long long)blockIdx.x * COOP_WARPS + wib; v < cnt; v += nw) {
+            const long long q = v / COOP_LIST_SPLIT;
+            const int k = (int)(v - q * COOP_LIST_SPLIT);
+            const int2 e = a.qlist[(list_base(a) + q) * a.qdir];
+            const PairHdr B = a.pairs[e.x];
+            const PairHdr K = a.pairs[e.y];
+            const int npq = B.nprim * K.nprim;
+            const int nch = min(COOP_LIST_SPLIT, (npq + 31) / 32);
+            if (k >= nch) continue;
+            const int chunk = (npq + nch - 1) / nch;
+            const int p0 = k * chunk, p1 = min(npq, p0 + chunk);
+            coop_task<R>(a, C, e.x, e.y, p0, p1, B, K, coef, Sb, V, Db, hc, lane, nq, np);
             __syncwarp();
-            for (int q = 0; q < cnt; ++q) {
-                if (lane <= C.L) V[lane] = Sb[q * (LTOT_MAX + 1) + lane];
-                __syncwarp();
-                const R* cf = coef + q * COOP_NCOEF;
-                int4 Gn = __ldg(C.vgrp);
-                for (int g = 0; g < C.nvg;) {
-                    const int4 G = Gn;
-                    // the next group of the same level is independent: evaluate both
-                    const bool pair = !G.w && g + 1 < C.nvg;
-                    const int4 G2 = pair ? __ldg(C.vgrp + g + 1) : G;
-                    const int gn = g + (pair ? 2 : 1);
-                    if (gn < C.nvg) Gn = __ldg(C.vgrp + gn);
-                    R v1 = R(0), v2 = R(0);
-                    int o1 = -1, o2 = -1;
-                    if (lane < G.y) o1 = coop_node<R>(G.x, __ldg(C.vdesc + G.z + lane), cf, V, v1);
-                    if (pair && lane < G2.y) o2 = coop_node<R>(G2.x, __ldg(C.vdesc + G2.z + lane), cf, V, v2);
-                    if (o1 >= 0) V[o1] = v1;
-                    if (o2 >= 0) V[o2] = v2;
-                    if ((pair ? G2.w : G.w)) __syncwarp();
-                    g = gn;
-                }
-#pragma unroll
-                for (int k = 0; k < COOP_MAXACC; ++k) {
-                    const int tt = lane + 32 * k;
-                    if (tt < C.nacc) acc[k] += V[__ldg(C.tgt + tt)];
-                }
-                __syncwarp();
-            }
-            if (lane == 0) { nq += (base == 0); np += cnt; }
         }
-
-        // ---- horizontal recurrence on the contracted block
-#pragma unroll
-        for (int k = 0; k < COOP_MAXACC; ++k) {
-            const int tt = lane + 32 * k;
-            if (tt < C.nacc) V[C.N + tt] = acc[k];
+    } else {
+        const int w = blockIdx.x * COOP_WARPS + wib;
+        if (w < a.ntasks) {
+            const int4 t = a.tasks[w];
+            const PairHdr B = a.pairs[t.x];
+            const PairHdr K = a.pairs[t.y];
+            if (coop_selected(a, B, K, t.x, t.y))
+                coop_task<R>(a, C, t.x, t.y, t.z, t.w, B, K, coef, Sb, V, Db, hc, lane, nq, np);
         }
-        coop_hrr_digest<R>(C, V, Db, hc, B, K, ib, j, a, lane);
     }
     if (a.counters) {
 #pragma unroll

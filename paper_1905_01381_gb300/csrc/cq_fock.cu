@@ -18,6 +18,7 @@
 #include <cstring>
 
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "cq_internal.h"
@@ -117,10 +118,12 @@ __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restric
 
 __global__ void counter_total_kernel(unsigned long long* c)
 {
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < 6) {
         unsigned long long t = 0;
-        for (int q = 0; q < NQC; ++q) t += c[4 + 4 * q + threadIdx.x];
-        c[threadIdx.x] = t;   // [0] fp64 quartets [1] fp64 prims [2] fp32 quartets [3] fp32 prims
+        for (int q = 0; q < NQC; ++q) t += c[6 + 6 * q + threadIdx.x];
+        // [0] fp64 quartets [1] fp64 prims [2] fp32 quartets [3] fp32 prims
+        // [4] double-float quartets [5] double-float prims
+        c[threadIdx.x] = t;
     }
 }
 
@@ -145,7 +148,7 @@ int ensure_scratch(cq_basis* b, int nk)
 
 // Screening and precision split of the candidates of one static task:
 // returns this lane's class of candidate j0 + lane (-1 rejected, 0 FP64,
-// 1 FP32).
+// 1 FP32, 2 double-float).
 __device__ __forceinline__ int classify_one(const ClassifyArgs& c, const float* Dm, int j, int jend, int ba, int bb,
                                             float Qb, float dab, int mode)
 {
@@ -157,15 +160,18 @@ __device__ __forceinline__ int classify_one(const ClassifyArgs& c, const float* 
     m = fmaxf(m, fmaxf(__ldg(Dm + bb * ns + kc), __ldg(Dm + bb * ns + kd)));
     const float bound = Qb * __ldg(c.Q + j) * m;
     if (!(bound >= c.tau)) return -1;
-    return ((mode & 1) && bound < c.tau_mixed) ? 1 : 0;
+    if (!(mode & 1)) return 0;
+    if (bound < c.tau_mixed) return 1;
+    return bound < c.tau_64 ? 2 : 0;
 }
 
-// Pass 1 (write = 0): survivors per task and precision -> tcount[2t + p].
+// Pass 1 (write = 0): survivors per task and precision -> tcount[3t + p].
 // Pass 3 (write = 1): survivors written at the scanned offsets, in task
 // order and, within a task, in ket order, so that a warp of the integral
 // kernels gets consecutive kets of mostly one bra with similar primitive
 // counts.  FP64 entries fill a class's region from the front, FP32 entries
-// from the back.
+// from the back, double-float entries follow the FP64 ones (their base is
+// the class's FP64 total from the scan).
 __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsigned int* __restrict__ tcount,
                                 const unsigned int* __restrict__ toff)
 {
@@ -183,8 +189,9 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
     const float dab = __ldg(Dm + ba * c.nsh + bb);
     const int mode = c.mol_mode ? (__ldg(c.mol_mode + smb / c.lds2) & (c.split ? 3 : 2)) : (c.split ? 1 : 0);
     const long long base = c.cls_qoff[qc], top = c.cls_qoff[qc + 1];
-    unsigned int n0 = 0, n1 = 0;
-    unsigned int o0 = write ? toff[2 * w] : 0, o1 = write ? toff[2 * w + 1] : 0;
+    unsigned int n0 = 0, n1 = 0, n2 = 0;
+    unsigned int o0 = write ? toff[3 * w] : 0, o1 = write ? toff[3 * w + 1] : 0;
+    unsigned int o2 = write ? toff[3 * w + 2] + c.qcount[3 * qc] : 0;
     // a skipped molecule's task has no survivors (the whole warp agrees)
     const int jend = (mode & 2) ? t.y : t.z;
     for (int j0 = t.y; j0 < jend; j0 += 32) {
@@ -192,17 +199,21 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
         const int prec = classify_one(c, Dm, j, t.z, ba, bb, Qb, dab, mode);
         const unsigned m0 = __ballot_sync(0xffffffffu, prec == 0);
         const unsigned m1 = __ballot_sync(0xffffffffu, prec == 1);
+        const unsigned m2 = __ballot_sync(0xffffffffu, prec == 2);
         if (write) {
             const unsigned below = (1u << lane) - 1u;
             if (prec == 0) c.qlist[base + o0 + n0 + __popc(m0 & below)] = make_int2(ib, j);
             if (prec == 1) c.qlist[top - 1 - (o1 + n1 + __popc(m1 & below))] = make_int2(ib, j);
+            if (prec == 2) c.qlist[base + o2 + n2 + __popc(m2 & below)] = make_int2(ib, j);
         }
         n0 += __popc(m0);
         n1 += __popc(m1);
+        n2 += __popc(m2);
     }
     if (!write && lane == 0) {
-        tcount[2 * w] = n0;
-        tcount[2 * w + 1] = n1;
+        tcount[3 * w] = n0;
+        tcount[3 * w + 1] = n1;
+        tcount[3 * w + 2] = n2;
     }
 }
 
@@ -211,31 +222,32 @@ __global__ void classify_kernel(const ClassifyArgs c, int nqc, int write, unsign
 __device__ __forceinline__ void scan_range(int t0, int t1, const unsigned int* __restrict__ tcount,
                                           unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
 {
-    __shared__ unsigned int part[2][1024];
+    __shared__ unsigned int part[3][1024];
     const int n = t1 - t0;
     const int per = (n + blockDim.x - 1) / blockDim.x;
     const int b0 = t0 + threadIdx.x * per, b1 = min(t1, b0 + per);
-    unsigned int s0 = 0, s1 = 0;
-    for (int t = b0; t < b1; ++t) { s0 += tcount[2 * t]; s1 += tcount[2 * t + 1]; }
-    part[0][threadIdx.x] = s0;
-    part[1][threadIdx.x] = s1;
+    unsigned int sp[3] = {0, 0, 0};
+    for (int t = b0; t < b1; ++t)
+        for (int p = 0; p < 3; ++p) sp[p] += tcount[3 * t + p];
+    for (int p = 0; p < 3; ++p) part[p][threadIdx.x] = sp[p];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned int a0 = 0, a1 = 0;
+    if (threadIdx.x < 3) {
+        const int p = threadIdx.x;
+        unsigned int acc = 0;
         for (int i = 0; i < (int)blockDim.x; ++i) {
-            const unsigned int x0 = part[0][i], x1 = part[1][i];
-            part[0][i] = a0; part[1][i] = a1;
-            a0 += x0; a1 += x1;
+            const unsigned int x = part[p][i];
+            part[p][i] = acc;
+            acc += x;
         }
-        qcount[0] = a0;
-        qcount[1] = a1;
+        qcount[p] = acc;
     }
     __syncthreads();
-    unsigned int a0 = part[0][threadIdx.x], a1 = part[1][threadIdx.x];
-    for (int t = b0; t < b1; ++t) {
-        toff[2 * t] = a0; toff[2 * t + 1] = a1;
-        a0 += tcount[2 * t]; a1 += tcount[2 * t + 1];
-    }
+    unsigned int ap[3] = {part[0][threadIdx.x], part[1][threadIdx.x], part[2][threadIdx.x]};
+    for (int t = b0; t < b1; ++t)
+        for (int p = 0; p < 3; ++p) {
+            toff[3 * t + p] = ap[p];
+            ap[p] += tcount[3 * t + p];
+        }
 }
 
 // Pass 2: per class (one CTA each), the scan over the class's tasks.
@@ -243,7 +255,7 @@ __global__ void scan_tasks_kernel(const int* __restrict__ cls_task_off, const un
                                   unsigned int* __restrict__ toff, unsigned int* __restrict__ qcount)
 {
     const int qc = blockIdx.x;
-    scan_range(cls_task_off[qc], cls_task_off[qc + 1], tcount, toff, qcount + 2 * qc);
+    scan_range(cls_task_off[qc], cls_task_off[qc + 1], tcount, toff, qcount + 3 * qc);
 }
 
 // The same over the n tasks of one pass (one CTA).
@@ -251,6 +263,31 @@ __global__ void scan_pass_kernel(int n, const unsigned int* __restrict__ tcount,
                                  unsigned int* __restrict__ qcount)
 {
     scan_range(0, n, tcount, toff, qcount);
+}
+
+// Precisions a build evaluates: FP64 only, FP64 + FP32, or FP64 + FP32 +
+// double-float (mixed builds with fp64_tol above mixed_tol).
+static int n_precisions(const cq_fock_opts& o)
+{
+    if (o.prec == CQ_PREC_FP64) return 1;
+    return o.fp64_tol > o.mixed_tol ? 3 : 2;
+}
+
+// List and screening arguments of precision pp of one class: FP64 entries
+// from the front of the class's region, FP32 from the back, double-float
+// after the FP64 ones; qcnt points at the class's three survivor counts.
+static void set_precision(JKArgs& a, const cq_fock_opts& o, int pp, int2* region, int2* region_last,
+                          unsigned int* qcnt)
+{
+    const bool three = n_precisions(o) == 3;
+    a.tier3 = three;
+    a.grid_cap = 0;
+    a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : (pp == 0 ? 1 : 2);   // cooperative kernel's own screening
+    a.tau_mixed = (float)((pp == 0 && three) ? o.fp64_tol : o.mixed_tol);
+    a.qlist = pp == 1 ? region_last : region;
+    a.qdir = pp == 1 ? -1 : 1;
+    a.qcount = qcnt + pp;
+    a.qbase = pp == 2 ? qcnt : nullptr;
 }
 
 static const int CLASS_ORDER[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
@@ -263,8 +300,8 @@ static int launch_passes(const cq_basis* b, JKArgs& a, ClassifyArgs c, const cq_
 {
     cq_basis* bm = const_cast<cq_basis*>(b);
     const long long cap = std::min<long long>(b->list_cap, 1LL << 30);
-    c.cls_qoff = b->d_pass_qoff;   // FP64 entries from the front, FP32 from the back of the list
-    const int npp = o.prec == CQ_PREC_FP64 ? 1 : 2;
+    c.cls_qoff = b->d_pass_qoff;   // FP64 (then double-float) entries from the front, FP32 from the back
+    const int npp = n_precisions(o);
     for (int oi = 0; oi < NQC; ++oi) {
         const int qc = CLASS_ORDER[oi];
         const int t0 = b->task_off[qc], t1 = b->task_off[qc + 1];
@@ -286,20 +323,18 @@ static int launch_passes(const cq_basis* b, JKArgs& a, ClassifyArgs c, const cq_
             c.tasks = b->d_tasks + ta;
             c.ntasks = tb - ta;
             const int blocks = (int)(((long long)c.ntasks * 32 + 255) / 256);
-            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 0, b->d_tcount + 2 * (size_t)ta, nullptr);
-            scan_pass_kernel<<<1, 1024, 0, s>>>(c.ntasks, b->d_tcount + 2 * (size_t)ta, b->d_toff + 2 * (size_t)ta,
-                                                b->d_qcount + 2 * qc);
-            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 1, nullptr, b->d_toff + 2 * (size_t)ta);
+            c.qcount = b->d_qcount + 3 * qc;   // the pass's counts (read as class 0 of one)
+            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 0, b->d_tcount + 3 * (size_t)ta, nullptr);
+            scan_pass_kernel<<<1, 1024, 0, s>>>(c.ntasks, b->d_tcount + 3 * (size_t)ta, b->d_toff + 3 * (size_t)ta,
+                                                b->d_qcount + 3 * qc);
+            classify_kernel<<<blocks, 256, 0, s>>>(c, 1, 1, nullptr, b->d_toff + 3 * (size_t)ta);
             a.tasks = c.tasks;
             a.ntasks = c.ntasks;
             a.qmax = cand;
             for (int pp = 0; pp < npp; ++pp) {
-                a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
-                a.qlist = pp == 0 ? b->d_qlist : b->d_qlist + (b->list_cap - 1);
-                a.qdir = pp == 0 ? 1 : -1;
-                a.qcount = b->d_qcount + 2 * qc + pp;
+                set_precision(a, o, pp, b->d_qlist, b->d_qlist + (b->list_cap - 1), b->d_qcount + 3 * qc);
                 unsigned long long* base_cnt = a.counters;
-                a.counters = base_cnt + 4 * qc + 2 * pp;
+                a.counters = base_cnt + 6 * qc + 2 * pp;
                 cudaEvent_t* ev = nullptr;
                 if (profile) {   // one event pair per pass, summed by cq_fock_class_stats
                     auto& v = bm->pev_pass[qc][pp];
@@ -337,7 +372,8 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     c.pairs = b->d_pairs; c.tasks = b->d_tasks; c.ntasks = b->task_off[NQC];
     c.cls_task_off = b->d_task_off; c.cls_qoff = b->d_qoff;
     c.Q = a.Q; c.Dmax = a.Dmax; c.nsh = b->lds;
-    c.tau = a.tau; c.tau_mixed = a.tau_mixed; c.split = o.prec == CQ_PREC_MIXED;
+    c.tau = a.tau; c.tau_mixed = (float)o.mixed_tol; c.split = o.prec == CQ_PREC_MIXED;
+    c.tau_64 = n_precisions(o) == 3 ? (float)o.fp64_tol : 0.f;
     c.qlist = b->d_qlist; c.qcount = b->d_qcount;
     if (b->passes) return launch_passes(b, a, c, o, profile, s);
     if (c.ntasks > 0) {
@@ -369,13 +405,11 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
         if (a.ntasks == 0 || a.qmax == 0) continue;
         a.ket_end = b->cls_off[Y + 1];
         a.same_class = (X == Y);
-        for (int pp = 0; pp < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++pp) {
-            a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : 1 + pp;
-            a.qlist = pp == 0 ? b->d_qlist + b->qoff[qc] : b->d_qlist + (b->qoff[qc + 1] - 1);
-            a.qdir = pp == 0 ? 1 : -1;
-            a.qcount = b->d_qcount + 2 * qc + pp;
+        for (int pp = 0; pp < n_precisions(o); ++pp) {
+            set_precision(a, o, pp, b->d_qlist + b->qoff[qc], b->d_qlist + (b->qoff[qc + 1] - 1),
+                          b->d_qcount + 3 * qc);
             unsigned long long* base_cnt = a.counters;
-            a.counters = base_cnt + 4 * qc + 2 * pp;
+            a.counters = base_cnt + 6 * qc + 2 * pp;
             if (profile) {
                 for (int e = 0; e < 2; ++e)
                     if (!bm->pev[qc][pp][e]) CQ_CUDA(cudaEventCreate(&bm->pev[qc][pp][e]));
@@ -399,26 +433,58 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     return CQ_OK;
 }
 
-void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int fp32, cudaStream_t s)
+static int class_L(int qc)
 {
-    if (b->variant[qc][fp32] == VARIANT_SYM && SYM_LAUNCH[qc] && (fp32 || SYM_F64[qc])) {
-        SYM_LAUNCH[qc](a, fp32, s);
-        return;
+    int X = 0;
+    while ((X + 1) * (X + 2) / 2 <= qc) ++X;
+    const int Y = qc - X * (X + 1) / 2;
+    return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
+}
+
+static void launch_coop_list(const JKArgs& a, int qc, int prec, cudaStream_t s)
+{
+    JKArgs c = a;
+    c.coop_list = 1;
+    c.ntasks = (int)std::min<long long>(a.qmax, INT_MAX);
+    if (c.ntasks > 0) launch_coop(c, qc, prec, s);
+}
+
+// Whether class qc has kernel variant v at precision prec (0 FP64, 1 FP32,
+// 2 double-float).  The cooperative kernel's task mode screens inside the
+// kernel against one bound, so the double-float band takes it on the
+// screened list only.
+bool variant_exists(int qc, int prec, int v)
+{
+    switch (v) {
+    case VARIANT_LANES: return prec != PREC_DF || LANE_DF[qc];
+    case VARIANT_COOP: return prec != PREC_DF;
+    case VARIANT_SYM: return SYM_LAUNCH[qc] != nullptr && (prec == 1 || SYM_F64[qc]);
+    case VARIANT_COOP_LIST: return true;
+    default: return false;
     }
-    // a class switched to the cooperative kernel uses it once its task list
-    // has been rebuilt (by the next cq_fock_build); until then, lane groups
-    if (b->variant[qc][fp32] == VARIANT_COOP && b->coop_list && !b->coop_dirty) {
-        JKArgs c = a;
-        c.coop_list = 1;
-        c.ntasks = (int)a.qmax;
-        if (c.ntasks > 0) launch_coop(c, qc, fp32, s);
-    } else if (b->variant[qc][fp32] == VARIANT_COOP && !b->coop_dirty) {
+}
+
+void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int prec, cudaStream_t s)
+{
+    int v = b->variant[qc][prec];
+    if (!variant_exists(qc, prec, v)) v = VARIANT_COOP_LIST;
+    if (v == VARIANT_SYM) {
+        SYM_LAUNCH[qc](a, prec, s);
+    } else if (v == VARIANT_LANES) {
+        JK_LAUNCH[qc](a, prec, s);
+    } else if (v == VARIANT_COOP_LIST || (b->coop_list && !b->coop_dirty)) {
+        // the screened list (large bases always), each quartet split over up
+        // to four warps
+        launch_coop_list(a, qc, prec, s);
+    } else if (!b->coop_dirty) {
         JKArgs c = a;
         c.tasks = b->d_coop_tasks + b->coop_off[qc];
         c.ntasks = b->coop_off[qc + 1] - b->coop_off[qc];
-        if (c.ntasks > 0) launch_coop(c, qc, fp32, s);
+        if (c.ntasks > 0) launch_coop(c, qc, prec, s);
     } else {
-        JK_LAUNCH[qc](a, fp32, s);
+        // a class switched to the cooperative kernel uses it once its task
+        // list has been rebuilt (by the next cq_fock_build); until then, lane groups
+        JK_LAUNCH[qc](a, prec, s);
     }
 }
 
@@ -455,28 +521,28 @@ extern "C" int cq_set_list_capacity(long long entries)
 
 extern "C" long long cq_get_list_capacity(void) { return g_list_capacity; }
 
-extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int fp32, int variant)
+extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int prec, int variant)
 {
-    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1 || variant < 0 || variant > 2) {
+    if (!b || qc < 0 || qc >= NQC || prec < 0 || prec > 2 || variant < 0 || variant >= NVARIANT) {
         set_error("cq_fock_set_variant: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
-    if (variant == VARIANT_SYM && (!SYM_LAUNCH[qc] || (!fp32 && !SYM_F64[qc]))) {
-        set_error("cq_fock_set_variant: this class and precision have no axis-permutation kernel");
+    if (!variant_exists(qc, prec, variant)) {
+        set_error("cq_fock_set_variant: this class and precision have no such kernel variant");
         return CQ_ERR_UNSUPPORTED;
     }
-    if (b->variant[qc][fp32] != variant) b->coop_dirty = true;
-    b->variant[qc][fp32] = variant;
+    if (b->variant[qc][prec] != variant) b->coop_dirty = true;
+    b->variant[qc][prec] = variant;
     return CQ_OK;
 }
 
-extern "C" int cq_fock_get_variant(const cq_basis* b, int qc, int fp32, int* variant)
+extern "C" int cq_fock_get_variant(const cq_basis* b, int qc, int prec, int* variant)
 {
-    if (!b || !variant || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1) {
+    if (!b || !variant || qc < 0 || qc >= NQC || prec < 0 || prec > 2) {
         set_error("cq_fock_get_variant: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
-    *variant = b->variant[qc][fp32];
+    *variant = b->variant[qc][prec];
     return CQ_OK;
 }
 
@@ -497,7 +563,7 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
         set_error("cq_fock_build: unknown density kind");
         return CQ_ERR_INVALID_ARG;
     }
-    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1};
+    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1, 0.0};
     if (opts) o = *opts;
     if ((o.want_J && !J) || (o.want_K && !K)) {
         set_error("cq_fock_build: requested output pointer is NULL");
@@ -507,7 +573,7 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
         set_error("cq_fock_build: unknown precision mode");
         return CQ_ERR_INVALID_ARG;
     }
-    if (!(o.schwarz_tol >= 0.0) || !(o.mixed_tol >= 0.0)) {
+    if (!(o.schwarz_tol >= 0.0) || !(o.mixed_tol >= 0.0) || !(o.fp64_tol >= 0.0)) {
         set_error("cq_fock_build: negative threshold");
         return CQ_ERR_INVALID_ARG;
     }
@@ -527,7 +593,7 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
                                                               b->d_Dmax);
     CQ_CUDA(cudaMemsetAsync(b->d_Jp, 0, 2 * nn * sizeof(acc_t), s));
     CQ_CUDA(cudaMemsetAsync(b->d_Kp, 0, 2 * nn * nk * sizeof(acc_t), s));
-    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
+    CQ_CUDA(cudaMemsetAsync(b->d_cnt, 0, CNT_WORDS * sizeof(unsigned long long), s));
     if (b->profile) {
         memset(b->pev_used, 0, sizeof b->pev_used);
         memset(b->pev_npass, 0, sizeof b->pev_npass);
@@ -543,7 +609,8 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
     a.want_j = o.want_J; a.want_k = o.want_K;
     a.J = b->d_Jp; a.K = b->d_Kp;
     a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
-    a.counters = b->d_cnt + 4;
+    a.counters = b->d_cnt + 6;
+    a.primsx = b->d_primsx;
     a.mol_mode = mol_mode;
     a.lds2 = (long long)b->lds * b->lds;
     rc = classify_and_launch(b, a, o, b->profile != 0, s, mol_mode);
@@ -556,7 +623,7 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
     CQ_CUDA(cudaGetLastError());
     if (stats) {
         CQ_CUDA(cudaEventRecord(b->ev1, s));
-        unsigned long long c[4];
+        unsigned long long c[6];
         CQ_CUDA(cudaMemcpyAsync(c, b->d_cnt, sizeof c, cudaMemcpyDeviceToHost, s));
         CQ_CUDA(cudaStreamSynchronize(s));
         float ms = 0.f;
@@ -565,6 +632,8 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
         stats->prim_fp64 = c[1];
         stats->quartets_fp32 = c[2];
         stats->prim_fp32 = c[3];
+        stats->quartets_df = c[4];
+        stats->prim_df = c[5];
         stats->ms = ms;
     }
     return CQ_OK;
@@ -586,13 +655,13 @@ extern "C" int cq_fock_profile(cq_basis* b, int enable)
 extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, unsigned long long* quartets,
                                    unsigned long long* prims)
 {
-    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 1) {
+    if (!b || qc < 0 || qc >= NQC || fp32 < 0 || fp32 > 2) {
         set_error("cq_fock_class_stats: bad argument");
         return CQ_ERR_INVALID_ARG;
     }
     CQ_CUDA(cudaDeviceSynchronize());
     unsigned long long c[2];
-    CQ_CUDA(cudaMemcpy(c, b->d_cnt + 4 + 4 * qc + 2 * fp32, sizeof c, cudaMemcpyDeviceToHost));
+    CQ_CUDA(cudaMemcpy(c, b->d_cnt + 6 + 6 * qc + 2 * fp32, sizeof c, cudaMemcpyDeviceToHost));
     if (quartets) *quartets = c[0];
     if (prims) *prims = c[1];
     if (ms) {
@@ -624,35 +693,33 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
                            double* ms_out, void* stream)
 {
     if (!b || !P) { set_error("cq_autotune: NULL argument"); return CQ_ERR_INVALID_ARG; }
-    cq_fock_opts o{1e-14, 1e-3, CQ_PREC_MIXED, 1, 1};
+    cq_fock_opts o{1e-14, 1e-3, CQ_PREC_MIXED, 1, 1, 0.0};
     if (opts) o = *opts;
     const size_t nn = b->mstride;
     const int nk = nk_of(kind);
+    // precisions the build uses: FP64 alone, FP64 + FP32, or all three tiers
+    const int np = o.prec == CQ_PREC_FP64 ? 1 : n_precisions(o);
     double *J = nullptr, *K = nullptr;
     int rc;
     if ((rc = dalloc(&J, nn))) return rc;
     if ((rc = dalloc(&K, nn * (nk == 1 ? 1 : nk == 2 ? 2 : 8)))) { cudaFree(J); return rc; }
     const int old_profile = b->profile;
     b->profile = 1;
-    constexpr int NV = 3;
-    double t[NQC][2][NV];
+    double t[NQC][3][NVARIANT];
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p)
-            for (int v = 0; v < NV; ++v) t[q][p][v] = 1e300;
-    auto Lof = [](int qc) {
-        int X = 0;
-        while ((X + 1) * (X + 2) / 2 <= qc) ++X;
-        const int Y = qc - X * (X + 1) / 2;
-        return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
-    };
+        for (int p = 0; p < 3; ++p)
+            for (int v = 0; v < NVARIANT; ++v) t[q][p][v] = 1e300;
+    // the cooperative kernel is timed for total angular momentum >= 4 only;
+    // below that lane groups are always faster
     auto allowed = [&](int q, int p, int v) {
-        return v == VARIANT_LANES || (v == VARIANT_COOP && Lof(q) >= 4) ||
-               (v == VARIANT_SYM && SYM_LAUNCH[q] != nullptr && (p == 1 || SYM_F64[q]));
+        return variant_exists(q, p, v) && ((v != VARIANT_COOP && v != VARIANT_COOP_LIST) || class_L(q) >= 4);
     };
-    for (int v = 0; v < NV && rc == CQ_OK; ++v) {
+    // one round of builds per variant: every class that has the variant
+    // runs it, the others their default
+    for (int v = 0; v < NVARIANT && rc == CQ_OK; ++v) {
         for (int q = 0; q < NQC; ++q)
-            for (int p = 0; p < 2; ++p) {
-                const int want = allowed(q, p, v) ? v : VARIANT_LANES;
+            for (int p = 0; p < np; ++p) {
+                const int want = allowed(q, p, v) ? v : DEFAULT_VARIANT[q][p];
                 if (b->variant[q][p] != want) b->coop_dirty = true;
                 b->variant[q][p] = want;
             }
@@ -662,11 +729,11 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
         }
         if (rc) break;
         for (int q = 0; q < NQC; ++q)
-            for (int p = 0; p < 2; ++p) {
+            for (int p = 0; p < np; ++p) {
                 if (!allowed(q, p, v)) continue;
                 double ms = 0.0;
-                unsigned long long nq = 0, np = 0;
-                if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &np))) break;
+                unsigned long long nq = 0, npr = 0;
+                if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &npr))) break;
                 t[q][p][v] = ms;
             }
     }
@@ -676,14 +743,14 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
         cudaFree(K);
         return rc;
     }
-    int best[NQC][2], second[NQC][2];
+    int best[NQC][3], second[NQC][3];
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p) {
-            best[q][p] = VARIANT_LANES;
+        for (int p = 0; p < np; ++p) {
+            best[q][p] = DEFAULT_VARIANT[q][p];
             second[q][p] = -1;
-            for (int v = 1; v < NV; ++v)
+            for (int v = 0; v < NVARIANT; ++v)
                 if (t[q][p][v] < t[q][p][best[q][p]]) best[q][p] = v;
-            for (int v = 0; v < NV; ++v)
+            for (int v = 0; v < NVARIANT; ++v)
                 if (v != best[q][p] && t[q][p][v] < 1e299 &&
                     (second[q][p] < 0 || t[q][p][v] < t[q][p][second[q][p]]))
                     second[q][p] = v;
@@ -708,16 +775,16 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     };
     std::vector<std::pair<double, int>> cand;
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < (o.prec == CQ_PREC_FP64 ? 1 : 2); ++p)
-            if (second[q][p] >= 0) cand.push_back({t[q][p][best[q][p]], 2 * q + p});
+        for (int p = 0; p < np; ++p)
+            if (second[q][p] >= 0) cand.push_back({t[q][p][best[q][p]], 3 * q + p});
     std::sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
         return x.first > y.first;
     });
-    if (cand.size() > 6) cand.resize(6);
+    if (cand.size() > 8) cand.resize(8);
     double cur = 0.0;
     rc = build_ms(&cur);
     for (size_t i = 0; i < cand.size() && rc == CQ_OK; ++i) {
-        const int q = cand[i].second / 2, p = cand[i].second % 2;
+        const int q = cand[i].second / 3, p = cand[i].second % 3;
         const int keep = b->variant[q][p];
         b->variant[q][p] = second[q][p];
         b->coop_dirty = true;
@@ -734,9 +801,10 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     cudaFree(K);
     if (rc) return rc;
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < 2; ++p) {
-            if (table) table[2 * q + p] = b->variant[q][p];
-            if (ms_out) ms_out[2 * q + p] = t[q][p][best[q][p]] < 1e299 ? t[q][p][best[q][p]] : 0.0;
+        for (int p = 0; p < 3; ++p) {
+            const double ms = p < np ? t[q][p][best[q][p]] : 1e300;
+            if (table) table[3 * q + p] = b->variant[q][p];
+            if (ms_out) ms_out[3 * q + p] = ms < 1e299 ? ms : 0.0;
         }
     return ensure_coop_tasks(b);
 }

@@ -28,10 +28,17 @@ size_t coop_smem_bytes(int qc, int fp32);
 // kernel variant per quartet class: 0 lane-group kernel, 1 warp-cooperative,
 // 2 axis-permutation lane groups (classes with an entry in SYM_LAUNCH; FP64
 // where SYM_F64)
-constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1, VARIANT_SYM = 2;
+constexpr int VARIANT_LANES = 0, VARIANT_COOP = 1, VARIANT_SYM = 2, VARIANT_COOP_LIST = 3, NVARIANT = 4;
+// precision index of a class launch: 0 FP64, 1 FP32, 2 double-float
+constexpr int PREC_DF = 2;
+// counters of a build: 6 totals (quartets, primitive quartets of each
+// precision), then 6 per class
+constexpr int CNT_WORDS = 6 + 6 * NQC;
 extern const LaunchJK SYM_LAUNCH[NQC];      // NULL where a class has no split kernel
-extern const int SYM_F64[NQC];              // 1 where the split kernel also exists in FP64
-extern const int DEFAULT_VARIANT[NQC][2];
+extern const int SYM_F64[NQC];              // 1 where the split kernel also exists in FP64 and double-float
+extern const int LANE_DF[NQC];              // 1 where the lane-group kernel exists in double-float
+extern const int DEFAULT_VARIANT[NQC][3];   // [class][FP64, FP32, double-float]
+bool variant_exists(int qc, int prec, int v);
 
 void set_error(const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
@@ -87,6 +94,7 @@ struct cq_basis {
     cq::PairHdr* d_pairs = nullptr;
     cq::PrimPair* d_prims = nullptr;
     cq::PrimPairF* d_primsf = nullptr;
+    cq::PrimPairX* d_primsx = nullptr;
     int4* d_tasks = nullptr;
     float* d_Qf = nullptr;
     double* d_Qd = nullptr;
@@ -110,11 +118,11 @@ struct cq_basis {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     // optional per-class profile of the last build
     int profile = 0;
-    cudaEvent_t pev[cq::NQC][2][2] = {};
-    bool pev_used[cq::NQC][2] = {};
+    cudaEvent_t pev[cq::NQC][3][2] = {};   // [class][FP64, FP32, double-float][start, end]
+    bool pev_used[cq::NQC][3] = {};
     // builds in passes: one event pair per pass and precision of a class
-    std::vector<cudaEvent_t> pev_pass[cq::NQC][2];
-    int pev_npass[cq::NQC][2] = {};
+    std::vector<cudaEvent_t> pev_pass[cq::NQC][3];
+    int pev_npass[cq::NQC][3] = {};
     unsigned long long pcnt[cq::NQC][2][2] = {};
     // dense drivers (SCF, RT): library handles and cached one-electron data
     void* blas = nullptr;          // cublasHandle_t
@@ -134,7 +142,7 @@ struct cq_basis {
     int* d_info = nullptr;
     std::vector<void*> dense_bufs; // other driver scratch, freed with the basis
     void* rt = nullptr;            // RT-TDHF buffers (cq_drivers.cu)
-    int variant[cq::NQC][2] = {};  // kernel variant per class and precision
+    int variant[cq::NQC][3] = {};  // kernel variant per class and precision (FP64, FP32, double-float)
     // tasks of the warp-cooperative kernel: (bra, ket, primitive range), built
     // for the classes that use it, rebuilt when the variant table changes
     std::vector<int> coop_off;     // NQC + 1
@@ -142,11 +150,11 @@ struct cq_basis {
     // back of its region), rebuilt on the device by every build
     std::vector<long long> qoff;   // NQC + 1
     int2* d_qlist = nullptr;
-    unsigned int* d_qcount = nullptr;   // [NQC][2]
+    unsigned int* d_qcount = nullptr;   // [NQC][3]
     int* d_task_off = nullptr;          // NQC + 1 (device copy)
     long long* d_qoff = nullptr;        // NQC + 1 (device copy)
-    unsigned int* d_tcount = nullptr;   // 2 per task: survivors per precision
-    unsigned int* d_toff = nullptr;     // 2 per task: offsets in the class lists
+    unsigned int* d_tcount = nullptr;   // 3 per task: survivors per precision
+    unsigned int* d_toff = nullptr;     // 3 per task: offsets in the class lists
     // side streams for running the class kernels of a build concurrently
     static constexpr int NSIDE = 6;
     cudaStream_t side[NSIDE] = {};

@@ -2,6 +2,8 @@
 // pairs), one lane per contracted shell quartet.  Included by the generated
 // per-class translation units after the class's EriClass specialisation.
 #pragma once
+#include <type_traits>
+
 #include "cq_common.cuh"
 
 namespace cq {
@@ -13,6 +15,7 @@ struct JKArgs {
     const PairHdr* pairs;
     const PrimPair* prims;
     const PrimPairF* primsf;
+    const PrimPairX* primsx;      // double-float shadow of the pair data
     const int4* tasks;            // (bra pair, first ket candidate, end of candidates, 0)
     int ntasks;
     int ket_end;                  // end of the ket class range (exclusive)
@@ -21,7 +24,7 @@ struct JKArgs {
     const float* Dmax;            // nsh x nsh block maxima of |P| (all components)
     int nsh;
     float tau;                    // screening threshold
-    float tau_mixed;              // precision split
+    float tau_mixed;              // precision split (FP32 below)
     int prec_sel;                 // 0: every surviving quartet; 1: bound >= tau_mixed; 2: bound < tau_mixed
     const double* D;              // nk scaled density matrices, nbf x nbf each
     int nk;
@@ -35,26 +38,28 @@ struct JKArgs {
     unsigned long long* counters; // [0] quartets, [1] primitive quartets
     const int2* qlist;            // compacted (bra, ket) quartets of this class and precision
     const unsigned int* qcount;   // number of entries (device)
+    const unsigned int* qbase;    // optional device offset of the list's first entry (double-float
+                                  // lists start after the FP64 list of their region); NULL: 0
     int qdir;                     // +1: entries qlist[i]; -1: entries qlist[-i] (list filled from the back)
     long long qmax;               // capacity of the list (candidate quartets of the class)
     const int* mol_mode;          // optional per-molecule mode (see ClassifyArgs), read by the
     long long lds2;               // cooperative kernel, which screens its own tasks
     int coop_list;                // cooperative kernel: 1 = quartets from qlist (already screened)
+    int tier3;                    // build with a double-float tier (the FP64 lists hold only the
+                                  // largest bounds: short lists of deep quartets)
+    int grid_cap;                 // largest grid (CTAs) of this launch; 0: jk_grid_cap().  The
+                                  // kernels stride over their list, so any grid is correct; short
+                                  // lists get small grids that leave the SMs to the concurrent
+                                  // class kernels of the other streams
 };
 
 template <typename R>
 __device__ __forceinline__ R ldR(const double* p) { return (R)__ldg(p); }
 
-template <typename R>
-__device__ __forceinline__ void load_prim(const PrimPair* pd, const PrimPairF* pf, int i,
-                                          PrimPairT<R>& o);
-
 // The pair data of a primitive pair in 16-byte vector loads (a lane reads
 // its own pair, so the loads of a warp are scattered: fewer, wider loads
 // cost fewer L1 wavefronts).
-template <>
-__device__ __forceinline__ void load_prim<double>(const PrimPair* pd, const PrimPairF*, int i,
-                                                  PrimPairT<double>& o)
+__device__ __forceinline__ void load_prim_v(const PrimPair* pd, int i, PrimPairT<double>& o)
 {
     const double2* s = reinterpret_cast<const double2*>(pd + i);
     const double2 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3);
@@ -64,9 +69,7 @@ __device__ __forceinline__ void load_prim<double>(const PrimPair* pd, const Prim
     o.K = __ldg(reinterpret_cast<const double*>(s + 4));
 }
 
-template <>
-__device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPairF* pf, int i,
-                                                 PrimPairT<float>& o)
+__device__ __forceinline__ void load_prim_v(const PrimPairF* pf, int i, PrimPairT<float>& o)
 {
     const float4* s = reinterpret_cast<const float4*>(pf + i);
     const float4 a = __ldg(s), b = __ldg(s + 1);
@@ -74,6 +77,43 @@ __device__ __forceinline__ void load_prim<float>(const PrimPair*, const PrimPair
     o.P[0] = a.z; o.P[1] = a.w; o.P[2] = b.x;
     o.PA[0] = b.y; o.PA[1] = b.z; o.PA[2] = b.w;
     o.K = __ldg(reinterpret_cast<const float*>(s + 2));
+}
+
+__device__ __forceinline__ void load_prim_v(const PrimPairX* px, int i, PrimPairT<df>& o)
+{
+    const float4* s = reinterpret_cast<const float4*>(px + i);
+    const float4 a = __ldg(s), b = __ldg(s + 1), c = __ldg(s + 2), d = __ldg(s + 3);
+    const float2 e = __ldg(reinterpret_cast<const float2*>(s + 4));
+    o.zeta = df(a.x, a.y); o.oo2z = df(a.z, a.w);
+    o.P[0] = df(b.x, b.y); o.P[1] = df(b.z, b.w); o.P[2] = df(c.x, c.y);
+    o.PA[0] = df(c.z, c.w); o.PA[1] = df(d.x, d.y); o.PA[2] = df(d.z, d.w);
+    o.K = df(e.x, e.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_prim(const JKArgs& a, int i, PrimPairT<R>& o)
+{
+    if constexpr (sizeof(R) == 4) load_prim_v(a.primsf, i, o);
+    else if constexpr (std::is_same<R, df>::value) load_prim_v(a.primsx, i, o);
+    else load_prim_v(a.prims, i, o);
+}
+
+template <typename R>
+__device__ __forceinline__ R ldg_r(const R* p)
+{
+    if constexpr (std::is_same<R, df>::value) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        return df(v.x, v.y);
+    } else {
+        return __ldg(p);
+    }
+}
+
+// the list offset of a kernel's entries (double-float lists start after the
+// FP64 list of their class region)
+__device__ __forceinline__ long long list_base(const JKArgs& a)
+{
+    return a.qbase ? (long long)*a.qbase : 0;
 }
 
 // Per-primitive-quartet quantities of the vertical recurrence: prefactor
@@ -127,10 +167,10 @@ __device__ __forceinline__ void eri_quartet(const PairHdr& B, const PairHdr& K, 
     for (int i = 0; i < C::NACC; ++i) acc[i] = R(0);
     for (int ip = 0; ip < B.nprim; ++ip) {
         PrimPairT<R> bp;
-        load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+        load_prim<R>(a, B.poff + ip, bp);
         for (int jp = 0; jp < K.nprim; ++jp) {
             PrimPairT<R> kp;
-            load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+            load_prim<R>(a, K.poff + jp, kp);
             prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
         }
     }
@@ -315,7 +355,7 @@ template <typename T, int G>
 __device__ __forceinline__ T group_sum(T v)
 {
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = G / 2; o > 0; o >>= 1) v += shfl_xor_r(v, o);
     return v;
 }
 
@@ -333,6 +373,7 @@ struct ClassifyArgs {
     const float* Dmax;
     int nsh;
     float tau, tau_mixed;
+    float tau_64;                 // double-float tier for bounds in [tau_mixed, tau_64) (off if <= tau_mixed)
     int split;                    // 0: every survivor to the FP64 list
     // optional per-molecule mode (batched drivers): bit 0 allows the FP32
     // list for the molecule's quartets, bit 1 skips the molecule; NULL: every
@@ -340,7 +381,7 @@ struct ClassifyArgs {
     const int* mol_mode;
     long long lds2;               // shell-block slot size (smbase / lds2 = molecule)
     int2* qlist;
-    unsigned int* qcount;         // [NQC][2]
+    unsigned int* qcount;         // [NQC][3] survivors per precision: FP64, FP32, double-float
 };
 
 // Largest grid (CTAs) of a lane-group launch on the current device: the
@@ -364,7 +405,7 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
     if (w * S >= cnt) return;
     const long long idx = w * S + grp;
     const bool on = idx < cnt;
-    const int2 e = a.qlist[(on ? idx : w * S) * a.qdir];
+    const int2 e = a.qlist[(list_base(a) + (on ? idx : w * S)) * a.qdir];
     const PairHdr B = a.pairs[e.x];
     const PairHdr K = a.pairs[e.y];
     R acc[C::NACC];
@@ -376,10 +417,10 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
         if constexpr (G == 1) {
             for (int ip = 0; ip < B.nprim; ++ip) {
                 PrimPairT<R> bp;
-                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
+                load_prim<R>(a, B.poff + ip, bp);
                 for (int jp = 0; jp < nkp; ++jp) {
                     PrimPairT<R> kp;
-                    load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                    load_prim<R>(a, K.poff + jp, kp);
                     prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
                 }
             }
@@ -389,8 +430,8 @@ __device__ __forceinline__ void jk_chunk(const JKArgs& a, const long long w, con
             while (jp >= nkp) { jp -= nkp; ++ip; }
             for (int pq = sub; pq < tot; pq += G) {
                 PrimPairT<R> bp, kp;
-                load_prim<R>(a.prims, a.primsf, B.poff + ip, bp);
-                load_prim<R>(a.prims, a.primsf, K.poff + jp, kp);
+                load_prim<R>(a, B.poff + ip, bp);
+                load_prim<R>(a, K.poff + jp, kp);
                 prim_quartet<LA, LB, LC, LD, R>(bp, kp, a.boys_d, a.boys_f, acc);
                 jp += G;
                 while (jp >= nkp) { jp -= nkp; ++ip; }
@@ -559,8 +600,8 @@ __global__ void __launch_bounds__(JK_THREADS) schwarz_kernel(const JKArgs a, int
         for (int pq = sub; pq < tot; pq += G) {
             const int ip = pq / B.nprim, jp = pq - (pq / B.nprim) * B.nprim;
             PrimPairT<double> bp, kp;
-            load_prim<double>(a.prims, a.primsf, B.poff + ip, bp);
-            load_prim<double>(a.prims, a.primsf, B.poff + jp, kp);
+            load_prim<double>(a, B.poff + ip, bp);
+            load_prim<double>(a, B.poff + jp, kp);
             prim_quartet<LA, LB, LA, LB, double>(bp, kp, a.boys_d, a.boys_f, acc);
         }
     }

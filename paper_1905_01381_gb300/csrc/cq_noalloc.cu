@@ -77,7 +77,7 @@ extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
     const size_t nn = (size_t)nbf * nbf;
     return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
            round256(2 * nn * sizeof(acc_t)) + round256((size_t)nshell * nshell * sizeof(float)) +
-           round256((4 + 6 * NQC) * sizeof(unsigned long long));
+           round256(CNT_WORDS * sizeof(unsigned long long));
 }
 
 static size_t noalloc_bytes(const cq_basis* b, int kind)
@@ -86,7 +86,7 @@ static size_t noalloc_bytes(const cq_basis* b, int kind)
     const size_t nn = b->mstride;
     return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
            round256(2 * nn * sizeof(acc_t)) + round256((size_t)b->nmol * b->lds * b->lds * sizeof(float)) +
-           round256((4 + 6 * NQC) * sizeof(unsigned long long));
+           round256(CNT_WORDS * sizeof(unsigned long long));
 }
 
 extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, double* J, void* K,
@@ -97,14 +97,14 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
         set_error("cq_fock_build_noalloc: unknown density kind");
         return CQ_ERR_INVALID_ARG;
     }
-    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1};
+    cq_fock_opts o{1e-14, 1e-5, CQ_PREC_FP64, 1, 1, 0.0};
     if (opts) o = *opts;
     if ((o.want_J && !J) || (o.want_K && !K)) {
         set_error("cq_fock_build_noalloc: requested output pointer is NULL");
         return CQ_ERR_INVALID_ARG;
     }
     if ((o.prec != CQ_PREC_FP64 && o.prec != CQ_PREC_MIXED) || !(o.schwarz_tol >= 0.0) ||
-        !(o.mixed_tol >= 0.0)) {
+        !(o.mixed_tol >= 0.0) || !(o.fp64_tol >= 0.0)) {
         set_error("cq_fock_build_noalloc: bad options");
         return CQ_ERR_INVALID_ARG;
     }
@@ -136,7 +136,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     // the array keeps the previous call's contents: clear the accumulators
     CQ_CUDA(cudaMemsetAsync(Jp, 0, 2 * nn * sizeof(acc_t), s));
     CQ_CUDA(cudaMemsetAsync(Kp, 0, 2 * nn * nk * sizeof(acc_t), s));
-    CQ_CUDA(cudaMemsetAsync(cnt, 0, (4 + 6 * NQC) * sizeof(unsigned long long), s));
+    CQ_CUDA(cudaMemsetAsync(cnt, 0, CNT_WORDS * sizeof(unsigned long long), s));
     JKArgs a;
     memset(&a, 0, sizeof a);
     a.pairs = b->d_pairs; a.prims = b->d_prims; a.primsf = b->d_primsf;
@@ -148,7 +148,8 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     a.want_j = o.want_J; a.want_k = o.want_K;
     a.J = Jp; a.K = Kp;
     a.boys_d = b->d_boys; a.boys_f = b->d_boysf;
-    a.counters = cnt + 4;
+    a.counters = cnt + 6;
+    a.primsx = b->d_primsx;
     rc = classify_and_launch(b, a, o, false, s);
     if (rc) return rc;
     CQ_CUDA(cudaGetLastError());

@@ -34,17 +34,17 @@ __host__ __device__ constexpr size_t sym_warp_bytes(int nslots)
 // result is component p[x] of the stored pair (scalar loads at permuted
 // offsets; cheaper here than vector loads followed by selects).
 template <typename R>
-__device__ __forceinline__ void load_prim_perm(const PrimPair* pd, const PrimPairF* pf, int i, int p0, int p1,
-                                               int p2, PrimPairT<R>& o)
+__device__ __forceinline__ void load_prim_perm(const JKArgs& a, int i, int p0, int p1, int p2, PrimPairT<R>& o)
 {
     const R* s;
-    if constexpr (sizeof(R) == 8) s = reinterpret_cast<const R*>(pd + i);
-    else s = reinterpret_cast<const R*>(pf + i);
-    o.zeta = __ldg(s + 0);
-    o.oo2z = __ldg(s + 1);
-    o.P[0] = __ldg(s + 2 + p0); o.P[1] = __ldg(s + 2 + p1); o.P[2] = __ldg(s + 2 + p2);
-    o.PA[0] = __ldg(s + 5 + p0); o.PA[1] = __ldg(s + 5 + p1); o.PA[2] = __ldg(s + 5 + p2);
-    o.K = __ldg(s + 8);
+    if constexpr (sizeof(R) == 4) s = reinterpret_cast<const R*>(a.primsf + i);
+    else if constexpr (std::is_same<R, df>::value) s = reinterpret_cast<const R*>(a.primsx + i);
+    else s = reinterpret_cast<const R*>(a.prims + i);
+    o.zeta = ldg_r(s + 0);
+    o.oo2z = ldg_r(s + 1);
+    o.P[0] = ldg_r(s + 2 + p0); o.P[1] = ldg_r(s + 2 + p1); o.P[2] = ldg_r(s + 2 + p2);
+    o.PA[0] = ldg_r(s + 5 + p0); o.PA[1] = ldg_r(s + 5 + p1); o.PA[2] = ldg_r(s + 5 + p2);
+    o.K = ldg_r(s + 8);
 }
 
 // H > 1: each of the G frames of a quartet is further split over H lanes
@@ -84,16 +84,16 @@ __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int
 #pragma unroll
         for (int i = 0; i < S::N0; ++i) acc[i] = R(0);
         if (on) {
-            const int2 e = a.qlist[idx * a.qdir];
+            const int2 e = a.qlist[(list_base(a) + idx) * a.qdir];
             const PairHdr B = a.pairs[e.x];
             const PairHdr K = a.pairs[e.y];
             if constexpr (H == 1) {
                 for (int ip = 0; ip < B.nprim; ++ip) {
                     PrimPairT<R> bp;
-                    load_prim_perm<R>(a.prims, a.primsf, B.poff + ip, p0, p1, p2, bp);
+                    load_prim_perm<R>(a, B.poff + ip, p0, p1, p2, bp);
                     for (int jp = 0; jp < K.nprim; ++jp) {
                         PrimPairT<R> kp;
-                        load_prim_perm<R>(a.prims, a.primsf, K.poff + jp, p0, p1, p2, kp);
+                        load_prim_perm<R>(a, K.poff + jp, p0, p1, p2, kp);
                         PrimQuartet<R> q;
                         prim_setup<L, R>(bp, kp, a.boys_d, a.boys_f, q);
                         S::template prim<R>(q, acc);
@@ -105,8 +105,8 @@ __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int
                 while (jp >= nkp) { jp -= nkp; ++ip; }
                 for (int pq = h; pq < tot; pq += H) {
                     PrimPairT<R> bp, kp;
-                    load_prim_perm<R>(a.prims, a.primsf, B.poff + ip, p0, p1, p2, bp);
-                    load_prim_perm<R>(a.prims, a.primsf, K.poff + jp, p0, p1, p2, kp);
+                    load_prim_perm<R>(a, B.poff + ip, p0, p1, p2, bp);
+                    load_prim_perm<R>(a, K.poff + jp, p0, p1, p2, kp);
                     PrimQuartet<R> q;
                     prim_setup<L, R>(bp, kp, a.boys_d, a.boys_f, q);
                     S::template prim<R>(q, acc);
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int
             for (int i = 0; i < S::N0; ++i) {
                 R v = acc[i];
 #pragma unroll
-                for (int o = H / 2; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, G * o);
+                for (int o = H / 2; o > 0; o >>= 1) v += shfl_down_r(v, G * o);
                 acc[i] = v;
             }
         }
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(SYM_THREADS) jk_sym_kernel(const JKArgs a, int
                 }
             }
             __syncwarp();
-            const int2 eg = a.qlist[gi * a.qdir];
+            const int2 eg = a.qlist[(list_base(a) + gi) * a.qdir];
             const PairHdr B = a.pairs[eg.x];
             const PairHdr K = a.pairs[eg.y];
             coop_hrr_digest<R>(C, V, Db, hc, B, K, eg.x, eg.y, a, lane);

@@ -1,10 +1,11 @@
 """Device Boys function and Schwarz table, element by element.
 
-* Boys: the device function the integral kernels call (cq_boys), in FP64
-  and in FP32 (FP64 below the first table interval), against the Boys
-  function's definition F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt evaluated by
+* Boys: the device function the integral kernels call (cq_boys), in FP64,
+  in FP32 (FP64 below the first table interval) and in double-float,
+  against the Boys function's definition F_m(T) = int_0^1 t^(2m) exp(-T t^2) dt evaluated by
   high-precision quadrature (tests/golden/boys_mpmath.txt) on T in [0, 200],
-  m <= 8: relative error <= 1e-14 in FP64 and <= 1e-6 in FP32.
+  m <= 8: relative error <= 1e-14 in FP64, <= 1e-13 in double-float
+  (48-bit words) and <= 1e-6 in FP32.
 * Schwarz (direct-SCF screening, Sec. "Reference Wave Functions"): the
   library's Q_ab = sqrt(max |(mn|mn)|) over the x^L-normalised functions of
   shells a, b, against the oracle's diagonal integrals over unit-normalised
@@ -49,7 +50,7 @@ def _golden():
     return np.array(T), ref
 
 
-@pytest.mark.parametrize("fp32,tol", [(False, 1e-14), (True, 1e-6)])
+@pytest.mark.parametrize("fp32,tol", [(0, 1e-14), (1, 1e-6), (2, 1e-13)])
 def test_device_boys_against_quadrature(cq, fp32, tol):
     import torch
     T, ref = _golden()

@@ -149,27 +149,30 @@ def test_zero_density_and_screening(cq):
 
 
 def _set_all(cq, b, variant):
-    """Every class and precision to `variant` where it exists (the
-    axis-permutation kernel, 2, exists for the classes of total angular
-    momentum >= 4 with a d shell and for (pp|pp), in FP64 too except (dd|dp)
-    and (dd|dd)); lane groups elsewhere."""
+    """Every class and precision (FP64, FP32, double-float) to `variant`
+    where it exists, the cooperative kernel on the screened list (3, which
+    every class has) elsewhere.  The axis-permutation kernel (2) exists for
+    the classes of total angular momentum >= 4 with a d shell and for
+    (pp|pp), in FP64 and double-float too except (dd|dp) and (dd|dd);
+    double-float lane groups (0) for total angular momentum <= 3; the
+    cooperative task mode (1) in FP64 and FP32."""
     n = 0
     for qc in range(21):
-        for p in (0, 1):
+        for p in (0, 1, 2):
             try:
                 b.set_variant(qc, p, variant)
-                n += variant == 2
+                n += 1
             except cq.CQError:
-                b.set_variant(qc, p, 0)
-    if variant == 2:
-        assert n == 13 + 11
+                b.set_variant(qc, p, 3)
+    assert n == {0: 42 + 8, 1: 42, 2: 13 + 11 + 11, 3: 63}[variant]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_every_class_in_each_kernel_variant(cq, orc, variant):
-    """Lane-group (0), warp-cooperative (1) and axis-permutation (2)
-    kernels for all 21 classes, FP64 and FP32 halves of the mixed build,
-    and an almost all-FP32 build against the oracle."""
+    """Lane-group (0), warp-cooperative (1: tasks, 3: screened list) and
+    axis-permutation (2) kernels for all 21 classes: FP64, the FP32 and FP64
+    halves of a mixed build, an almost all-FP32 build and an all
+    double-float build against the oracle."""
     mol, bas = CASES["OCNH3"]()
     b = cq.Basis(mol, bas)
     _set_all(cq, b, variant)
@@ -188,23 +191,37 @@ def test_every_class_in_each_kernel_variant(cq, orc, variant):
     assert st3["quartets_fp32"] > 10 * st3["quartets_fp64"]
     assert np.abs(J3.cpu().numpy() - Jo.real).max() < 2e-5
     assert np.abs(K3.cpu().numpy() - Ko).max() < 2e-5
+    # every quartet in double-float (~48 bits): the FP64 tolerance holds
+    Jd, Kd, std = b.fock_build(_gpu(P), prec=cq.CQ_PREC_MIXED, mixed_tol=0.0, fp64_tol=1e300, stats=True)
+    assert std["quartets_df"] == st["quartets_fp64"] + st["quartets_fp32"]
+    assert np.abs(Jd.cpu().numpy() - Jo.real).max() < TOL
+    assert np.abs(Kd.cpu().numpy() - Ko).max() < TOL
 
 
-def test_autotune_keeps_parity(cq, orc):
+@pytest.mark.parametrize("fp64_tol", [0.0, 1e-2])
+def test_autotune_keeps_parity(cq, orc, fp64_tol):
+    """The autotuner's choice (two tiers, or three with a double-float band
+    up to 1e-2) keeps FP64 and mixed builds at their tolerances."""
     mol, bas = CASES["OCNH3"]()
     b = cq.Basis(mol, bas)
     P = synth.density(b.nbf, 9, 16, complex_=True)
-    tab = b.autotune(_gpu(P), cache=False)
-    assert len(tab["variant"]) == 21
-    assert all(v in (0, 1, 2) for row in tab["variant"] for v in row)
+    tab = b.autotune(_gpu(P), mixed_tol=1e-4, fp64_tol=fp64_tol, cache=False)
+    assert len(tab["variant"]) == 21 and all(len(row) == 3 for row in tab["variant"])
+    assert all(v in (0, 1, 2, 3) for row in tab["variant"] for v in row)
     assert tab["variant"][19][0] != 2 and tab["variant"][20][0] != 2   # FP32-only there
+    assert all(row[2] != 1 for row in tab["variant"])                  # no double-float task mode
+    if fp64_tol:
+        assert any(ms > 0 for row in tab["best_ms"] for ms in row[2:])
     J, K = b.fock_build(_gpu(P))
     Jo, Ko = orc.jk(orc.OBasis(mol, bas), P)
     assert np.abs(J.cpu().numpy() - Jo.real).max() < TOL
     assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+    Jm, Km = b.fock_build(_gpu(P), prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, fp64_tol=fp64_tol)
+    assert np.abs(Jm.cpu().numpy() - Jo.real).max() < 1e-6
+    assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_bounded_list_passes(cq, orc, variant):
     """A basis whose candidate quartets exceed the list capacity builds in
     passes (one task per bra pair, the cooperative kernel reading the list):
@@ -232,7 +249,7 @@ def test_bounded_list_passes(cq, orc, variant):
     assert np.abs(Km.cpu().numpy() - Ko).max() < 1e-6
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed", "three-tier"])
 def test_builds_bitwise_reproducible(cq, prec):
     """J'/K' are accumulated as exact integers (order-independent), so two
     identical builds -- class kernels on concurrent streams, atomics in any
@@ -242,7 +259,8 @@ def test_builds_bitwise_reproducible(cq, prec):
     b = cq.Basis(mol, bas)
     n = b.nbf
     Pp = np.stack([synth.hermitian_component(n, 40 + i, scale=0.1) for i in range(4)])
-    kw = {"prec": cq.CQ_PREC_MIXED, "mixed_tol": 1e-4} if prec == "mixed" else {}
+    kw = {"mixed": {"prec": cq.CQ_PREC_MIXED, "mixed_tol": 1e-4},
+          "three-tier": {"prec": cq.CQ_PREC_MIXED, "mixed_tol": 1e-4, "fp64_tol": 1e-2}}.get(prec, {})
     for P in (synth.density(n, 9, 18), synth.density(n, 9, 19, complex_=True), Pp):
         outs = [b.fock_build(_gpu(P), **kw) for _ in range(3)]
         for J, K in outs[1:]:
@@ -252,3 +270,42 @@ def test_builds_bitwise_reproducible(cq, prec):
     b2 = cq.Basis(mol, bas)
     J2, K2 = b2.fock_build(_gpu(P), **kw)
     assert torch.equal(J2, outs[0][0]) and torch.equal(K2, outs[0][1])
+
+
+@pytest.mark.parametrize("name", ["OCNH3", "O1H2_deep"])
+def test_double_float_tier(cq, orc, name):
+    """The double-float tier: with every surviving quartet in double-float
+    (pairs of FP32 values, ~48 bits) J and K still match the FP64 oracle at
+    1e-10 for real, complex-Hermitian and Pauli densities; with three tiers
+    (FP32 below 1e-4, double-float up to 1e-2, FP64 above) all three lists
+    are used and the result matches at the mixed tolerance."""
+    mol, bas = CASES[name]()
+    b = cq.Basis(mol, bas)
+    ob = orc.OBasis(mol, bas)
+    n = b.nbf
+    D = synth.density(n, max(1, n // 4), 11)
+    J, K, st = b.fock_build(_gpu(D), prec=cq.CQ_PREC_MIXED, mixed_tol=0.0, fp64_tol=1e300, stats=True)
+    assert st["quartets_df"] > 0 and st["quartets_fp64"] == 0 and st["quartets_fp32"] == 0
+    Jo, Ko = orc.jk(ob, D)
+    assert np.abs(J.cpu().numpy() - Jo).max() < TOL
+    assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+    Pc = synth.density(n, max(1, n // 4), 12, complex_=True)
+    Jc, Kc = b.fock_build(_gpu(Pc), prec=cq.CQ_PREC_MIXED, mixed_tol=0.0, fp64_tol=1e300)
+    Joc, Koc = orc.jk(ob, Pc)
+    assert np.abs(Jc.cpu().numpy() - Joc.real).max() < TOL
+    assert np.abs(Kc.cpu().numpy() - Koc).max() < TOL
+    from oracle import drivers
+    Pp = np.ascontiguousarray(drivers.pauli_split(synth.spinor_density(n, 7, 13)))
+    Jp, Kp = b.fock_build(_gpu(Pp), prec=cq.CQ_PREC_MIXED, mixed_tol=0.0, fp64_tol=1e300)
+    Jop, _ = orc.jk(ob, Pp[0])
+    assert np.abs(Jp.cpu().numpy() - Jop.real).max() < TOL
+    for I in range(4):
+        _, KoI = orc.jk(ob, Pp[I])
+        assert np.abs(Kp.cpu().numpy()[I] - KoI).max() < TOL, I
+    J3, K3, st3 = b.fock_build(_gpu(D), prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, fp64_tol=1e-2, stats=True)
+    assert st3["quartets_df"] > 0 and st3["quartets_fp64"] > 0 and st3["quartets_fp32"] > 0
+    _, _, st2 = b.fock_build(_gpu(D), prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, stats=True)
+    assert st3["quartets_df"] + st3["quartets_fp64"] == st2["quartets_fp64"]
+    assert st3["quartets_fp32"] == st2["quartets_fp32"]
+    assert np.abs(J3.cpu().numpy() - Jo).max() < 1e-6
+    assert np.abs(K3.cpu().numpy() - Ko).max() < 1e-6

@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
 MIXED_TOL = 5e-3      # the benchmark's split of the rt16 build
+FP64_TOL = 0.1        # double-float below, FP64 above (the benchmark's three tiers)
 TOL_MIXED_ELEM = 5e-6
 
 
@@ -62,17 +63,18 @@ def _blk(M, bfo, a, b):
 
 def test_rt16_benchmark_configuration(cq, orc):
     """The 16-atom, 210-function workload with its complex-Hermitian
-    density, as the benchmark builds it (autotuned kernel variants): whole
-    blocks of 16 shell pairs, FP64 and mixed."""
+    density, as the benchmark builds it (autotuned kernel variants; FP32,
+    double-float and FP64 tiers): whole blocks of 16 shell pairs, FP64 and
+    mixed."""
     import torch
     mol, bas = synth.workload_rt16()
     b = cq.Basis(mol, bas)
     n = b.nbf
     Ph = synth.density(n, 29, 5, complex_=True)
     P = torch.as_tensor(Ph, device="cuda")
-    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, cache=False)
     J, K = b.fock_build(P)
-    Jm, Km = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL)
+    Jm, Km = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL)
     pairs = _pairs(b.nshell, 16, 3)
     ref = orc.jk_blocks(orc.OBasis(mol, bas), [Ph.real, Ph.imag], [p[0] for p in pairs], [p[1] for p in pairs])
     bfo = _bfo(bas)
@@ -100,8 +102,9 @@ def test_large100_mixed(cq, orc):
     assert n == 1930
     Ph = synth.density(n, 200, 11)
     P = torch.as_tensor(Ph, device="cuda")
-    J, K, st = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=3e-3, schwarz_tol=1e-12, stats=True)
-    assert st["quartets_fp32"] > 100 * st["quartets_fp64"] > 0
+    J, K, st = b.fock_build(P, prec=cq.CQ_PREC_MIXED, mixed_tol=3e-3, fp64_tol=FP64_TOL, schwarz_tol=1e-12,
+                            stats=True)
+    assert st["quartets_fp32"] > 100 * st["quartets_df"] > 0 and st["quartets_fp64"] > 0
     pairs = _pairs(b.nshell, 16, 4)
     ref = orc.jk_blocks(orc.OBasis(mol, bas), [Ph], [p[0] for p in pairs], [p[1] for p in pairs])
     bfo = _bfo(bas)
