@@ -230,6 +230,13 @@ int cq_fock_set_variant(cq_basis* b, int qc, int prec, int variant);
 
 int cq_fock_get_variant(const cq_basis* b, int qc, int prec, int* variant);
 
+/* Work split of variant 3 (the cooperative kernel on the screened list) at
+ * precision prec: each quartet's primitive quartets are cut into
+ * ceil(nprim / chunk) ranges, at most `split` (1..64), one warp task each
+ * (every task repeats the HRR and the digestion).  Defaults: FP64 8 / 64,
+ * FP32 and double-float 4 / 32.  CQ_ERR_INVALID_ARG out of range. */
+int cq_fock_set_list_split(cq_basis* b, int prec, int split, int chunk);
+
 /* Memory bound of the quartet lists (no paper counterpart).  A basis
  * created while the capacity is C keeps one list of min(C, candidates)
  * 8-byte entries, where candidates = the shell quartets of every class that
@@ -244,10 +251,10 @@ int cq_fock_get_variant(const cq_basis* b, int qc, int prec, int* variant);
 int cq_set_list_capacity(long long entries);
 long long cq_get_list_capacity(void);
 
-/* Autotuner: times every kernel variant a class has (the cooperative ones
- * for total angular momentum >= 4 only) at every precision the options use
- * (FP64; FP64 and FP32; or FP64, FP32 and double-float when fp64_tol >
- * mixed_tol) on the given density (device, layout as for cq_fock_build)
+/* Autotuner: times every kernel variant a class has at every precision
+ * the options use -- FP64; FP64 and FP32; or, when fp64_tol > mixed_tol,
+ * FP32 and double-float (the FP64 tier of a three-tier build always runs
+ * variant 3) -- on the given density (device, layout as for cq_fock_build)
  * with the given options (NULL: mixed precision, mixed_tol 1e-3), keeps the
  * fastest variant per class and precision in the basis, then tries the
  * runner-up variant of each of the eight costliest (class, precision)
@@ -255,7 +262,7 @@ long long cq_get_list_capacity(void);
  * (concurrent) builds gets more than 1 % faster.  Returns the choice in
  * table[3*qc + prec] and the best isolated kernel time in
  * ms_out[3*qc + prec] (0 for precisions not used; host arrays of 63, either
- * may be NULL).  Runs up to 35 builds; allocates and frees two output
+ * may be NULL).  Runs up to 39 builds; allocates and frees two output
  * buffers. */
 int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts,
                 int* table, double* ms_out, void* stream);

@@ -110,6 +110,7 @@ def lib():
         L.cq_guess_density.argtypes = [vp, vp, ip, ctypes.c_int, ctypes.c_int, vp, vp]
         L.cq_fock_set_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_get_variant.argtypes = [vp, ctypes.c_int, ctypes.c_int, ip]
+        L.cq_fock_set_list_split.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_build_noalloc.argtypes = [vp, ctypes.c_int, vp, vp, vp, ctypes.POINTER(FockOpts), vp]
         L.cq_fock_noalloc_scratch_bytes.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int]
         L.cq_fock_noalloc_scratch_bytes.restype = ctypes.c_size_t
@@ -431,6 +432,10 @@ class Basis:
         double-float): 0 lane groups, 1 cooperative (task mode), 2 axis
         permutation, 3 cooperative on the screened list."""
         check(lib().cq_fock_set_variant(self.h, int(qc), int(prec), int(variant)), "cq_fock_set_variant")
+
+    def set_list_split(self, prec, split, chunk):
+        """Work split of variant 3 at precision prec (cq_fock_set_list_split)."""
+        check(lib().cq_fock_set_list_split(self.h, int(prec), int(split), int(chunk)), "cq_fock_set_list_split")
 
     def get_variant(self, qc, prec):
         v = ctypes.c_int()

@@ -32,8 +32,10 @@ LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
 
 
 # classes without an axis-permutation kernel: their double-float tier runs
-# the lane-group kernel (one lane per quartet)
+# the lane-group kernel, DF_LANES lanes per quartet (the double-float lists
+# are short and their quartets deep: about 150 primitive quartets each)
 LANE_DF = ("0000", "1000", "1010", "1100", "1110", "2000", "2010", "2100")
+DF_LANES = 4
 
 # axis-permutation kernels: lanes per frame splitting the primitive quartets
 # (FP64 lists are the short, large-bound part of a mixed build)
@@ -74,7 +76,6 @@ def gen_sources():
     for qc, (X, Y) in enumerate(qclasses()):
         la, lb, lc, ld = X[0], X[1], Y[0], Y[1]
         cls = f"{la}{lb}{lc}{ld}"
-        G = LANES.get(cls, 1)
         head = [f"// generated by build.py: class ({cls})",
                 '#include "cq_common.cuh"',
                 "namespace cq {",
@@ -86,13 +87,14 @@ def gen_sources():
         if cls in LANE_DF:
             precs.append(("df", "df"))
         for R, tag in precs:
+            G = DF_LANES if tag == "df" else LANES.get(cls, 1)
             src = head + [
                 f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
                 "{",
                 f"    const long long warps = (a.qmax + {32 // G} - 1) / {32 // G};",
                 "    long long blocks = (warps * 32 + JK_THREADS - 1) / JK_THREADS;",
                 "    if (blocks == 0) return;",
-                "    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();",
+                "    const long long cap = jk_grid_cap();",
                 "    if (blocks > cap) blocks = cap;",
                 f"    jk_kernel<{la}, {lb}, {lc}, {ld}, {R}, {G}><<<(unsigned)blocks, JK_THREADS, 0, s>>>(a);",
                 "}"]
@@ -165,7 +167,7 @@ def gen_sources():
             "    const long long warps = (a.qmax + NGRP - 1) / NGRP;",
             "    long long blocks = (warps + WARPS - 1) / WARPS;",
             "    if (blocks == 0) return;",
-            "    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();",
+            "    const long long cap = jk_grid_cap();",
             "    if (blocks > cap) blocks = cap;",
             "    kern<<<(unsigned)blocks, SYM_THREADS, bytes, s>>>(a, qc, nslots);",
             "}",

@@ -17,10 +17,10 @@ static void launch_coop_t(const JKArgs& a, int qc, cudaStream_t s)
         cudaFuncSetAttribute(jk_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_done = 1;
     }
-    const long long tasks = (long long)a.ntasks * (a.coop_list ? COOP_LIST_SPLIT : 1);
+    const long long tasks = (long long)a.ntasks * (a.coop_list ? a.coop_split : 1);
     long long blocks = (tasks + COOP_WARPS - 1) / COOP_WARPS;
     if (blocks == 0) return;
-    const long long cap = a.grid_cap > 0 ? a.grid_cap : jk_grid_cap();
+    const long long cap = jk_grid_cap();
     if (a.coop_list && blocks > cap) blocks = cap;   // warps stride over the list
     jk_coop_kernel<R><<<(unsigned)blocks, COOP_THREADS, bytes, s>>>(a, qc, nslots);
 }

@@ -22,7 +22,6 @@ constexpr int COOP_WARPS = 2;
 constexpr int COOP_THREADS = 32 * COOP_WARPS;
 constexpr int COOP_NCOEF = 26;
 constexpr int COOP_MAXACC = 31;   // ceil(961 / 32)
-constexpr int COOP_LIST_SPLIT = 4; // list mode: warp tasks per quartet, at most
 
 struct CoopClass {
     int la, lb, lc, ld, L, nacc, N, nslots, nvg, nhg;

@@ -276,21 +276,23 @@ __global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_ker
     unsigned long long nq = 0, np = 0;
     if (a.coop_list) {
         // list mode: the warps stride over the screened quartets of the list,
-        // each split into up to COOP_LIST_SPLIT equal ranges of its primitive
-        // quartets (at least 32 each), one range per warp task, so that a
-        // short list of deep quartets still spreads over the GPU (grid sized
-        // for the list capacity, capped; short lists leave the extra warps
-        // idle at once)
-        const long long cnt = (long long)*a.qcount * COOP_LIST_SPLIT;
+        // each split into ranges of about a.coop_chunk primitive quartets
+        // (at most a.coop_split ranges), one range per warp task: a deep
+        // quartet (up to ~1300 primitive quartets) would otherwise hold one
+        // warp for the whole build, and a short list of deep quartets would
+        // leave most SMs idle.  Every range repeats the HRR and the
+        // digestion, which bounds the useful split.
+        const int split = a.coop_split;
+        const long long cnt = (long long)*a.qcount * split;
         const long long nw = (long long)gridDim.x * COOP_WARPS;
         for (long long v = (long long)blockIdx.x * COOP_WARPS + wib; v < cnt; v += nw) {
-            const long long q = v / COOP_LIST_SPLIT;
-            const int k = (int)(v - q * COOP_LIST_SPLIT);
+            const long long q = v / split;
+            const int k = (int)(v - q * split);
             const int2 e = a.qlist[(list_base(a) + q) * a.qdir];
             const PairHdr B = a.pairs[e.x];
             const PairHdr K = a.pairs[e.y];
             const int npq = B.nprim * K.nprim;
-            const int nch = min(COOP_LIST_SPLIT, (npq + 31) / 32);
+            const int nch = min(split, (npq + a.coop_chunk - 1) / a.coop_chunk);
             if (k >= nch) continue;
             const int chunk = (npq + nch - 1) / nch;
             const int p0 = k * chunk, p1 = min(npq, p0 + chunk);

@@ -280,14 +280,13 @@ static void set_precision(JKArgs& a, const cq_fock_opts& o, int pp, int2* region
                           unsigned int* qcnt)
 {
     const bool three = n_precisions(o) == 3;
-    a.tier3 = three;
-    a.grid_cap = 0;
     a.prec_sel = (o.prec == CQ_PREC_FP64) ? 0 : (pp == 0 ? 1 : 2);   // cooperative kernel's own screening
     a.tau_mixed = (float)((pp == 0 && three) ? o.fp64_tol : o.mixed_tol);
     a.qlist = pp == 1 ? region_last : region;
     a.qdir = pp == 1 ? -1 : 1;
     a.qcount = qcnt + pp;
     a.qbase = pp == 2 ? qcnt : nullptr;
+    a.fp64_tier = three && pp == 0;
 }
 
 static const int CLASS_ORDER[NQC] = {20, 19, 18, 17, 16, 14, 13, 15, 12, 11, 10, 9, 8, 7, 5, 6, 4, 3, 2, 1, 0};
@@ -441,10 +440,17 @@ static int class_L(int qc)
     return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
 }
 
-static void launch_coop_list(const JKArgs& a, int qc, int prec, cudaStream_t s)
+// Cooperative kernel on the screened list, split per the basis's list_split
+// and list_chunk.  The FP64 pipe of an SM runs at 1/62 of its FP32 rate, so
+// the deep quartets of short FP64 lists pay to be spread over many warps
+// (SMs); every task repeats the HRR and the digestion, which bounds the
+// useful split.
+static void launch_coop_list(const cq_basis* b, const JKArgs& a, int qc, int prec, cudaStream_t s)
 {
     JKArgs c = a;
     c.coop_list = 1;
+    c.coop_split = b->list_split[prec];
+    c.coop_chunk = b->list_chunk[prec];
     c.ntasks = (int)std::min<long long>(a.qmax, INT_MAX);
     if (c.ntasks > 0) launch_coop(c, qc, prec, s);
 }
@@ -467,7 +473,10 @@ bool variant_exists(int qc, int prec, int v)
 void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int prec, cudaStream_t s)
 {
     int v = b->variant[qc][prec];
-    if (!variant_exists(qc, prec, v)) v = VARIANT_COOP_LIST;
+    // the FP64 list of a three-tier build holds the few quartets of the
+    // largest bounds, mostly deep contractions: spread over the GPU, each
+    // split into primitive ranges (the per-SM FP64 rate is 1/62 of FP32's)
+    if (!variant_exists(qc, prec, v) || a.fp64_tier) v = VARIANT_COOP_LIST;
     if (v == VARIANT_SYM) {
         SYM_LAUNCH[qc](a, prec, s);
     } else if (v == VARIANT_LANES) {
@@ -475,7 +484,7 @@ void launch_jk_class(const cq_basis* b, const JKArgs& a, int qc, int prec, cudaS
     } else if (v == VARIANT_COOP_LIST || (b->coop_list && !b->coop_dirty)) {
         // the screened list (large bases always), each quartet split over up
         // to four warps
-        launch_coop_list(a, qc, prec, s);
+        launch_coop_list(b, a, qc, prec, s);
     } else if (!b->coop_dirty) {
         JKArgs c = a;
         c.tasks = b->d_coop_tasks + b->coop_off[qc];
@@ -533,6 +542,17 @@ extern "C" int cq_fock_set_variant(cq_basis* b, int qc, int prec, int variant)
     }
     if (b->variant[qc][prec] != variant) b->coop_dirty = true;
     b->variant[qc][prec] = variant;
+    return CQ_OK;
+}
+
+extern "C" int cq_fock_set_list_split(cq_basis* b, int prec, int split, int chunk)
+{
+    if (!b || prec < 0 || prec > 2 || split < 1 || split > 64 || chunk < 1) {
+        set_error("cq_fock_set_list_split: bad argument");
+        return CQ_ERR_INVALID_ARG;
+    }
+    b->list_split[prec] = split;
+    b->list_chunk[prec] = chunk;
     return CQ_OK;
 }
 
@@ -684,11 +704,10 @@ extern "C" int cq_fock_class_stats(cq_basis* b, int qc, int fp32, double* ms, un
 }
 
 // Autotuner: time every kernel variant of every class on the caller's
-// density (one profiled build per variant after a warm-up build), keep the
-// fastest per class and precision.  Light classes (total angular momentum
-// below 4) stay on lane groups: one contracted quartet per warp cannot pay
-// off there.  The axis-permutation kernel exists for the classes listed in
-// SYM_LAUNCH (FP64 where SYM_F64).
+// density (profiled builds run on one stream, so each class kernel is timed
+// alone), keep the fastest per class and precision, then refine on whole
+// (concurrent) builds.  The axis-permutation kernel exists for the classes
+// listed in SYM_LAUNCH (FP64 and double-float where SYM_F64).
 extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_opts* opts, int* table,
                            double* ms_out, void* stream)
 {
@@ -698,7 +717,9 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     const size_t nn = b->mstride;
     const int nk = nk_of(kind);
     // precisions the build uses: FP64 alone, FP64 + FP32, or all three tiers
+    // (whose FP64 tier always takes the cooperative kernel on the list)
     const int np = o.prec == CQ_PREC_FP64 ? 1 : n_precisions(o);
+    const int p0 = np == 3 ? 1 : 0;
     double *J = nullptr, *K = nullptr;
     int rc;
     if ((rc = dalloc(&J, nn))) return rc;
@@ -709,33 +730,30 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < 3; ++p)
             for (int v = 0; v < NVARIANT; ++v) t[q][p][v] = 1e300;
-    // the cooperative kernel is timed for total angular momentum >= 4 only;
-    // below that lane groups are always faster
-    auto allowed = [&](int q, int p, int v) {
-        return variant_exists(q, p, v) && ((v != VARIANT_COOP && v != VARIANT_COOP_LIST) || class_L(q) >= 4);
-    };
+    auto allowed = [&](int q, int p, int v) { return variant_exists(q, p, v); };
     // one round of builds per variant: every class that has the variant
     // runs it, the others their default
     for (int v = 0; v < NVARIANT && rc == CQ_OK; ++v) {
         for (int q = 0; q < NQC; ++q)
-            for (int p = 0; p < np; ++p) {
+            for (int p = p0; p < np; ++p) {
                 const int want = allowed(q, p, v) ? v : DEFAULT_VARIANT[q][p];
                 if (b->variant[q][p] != want) b->coop_dirty = true;
                 b->variant[q][p] = want;
             }
-        for (int rep = 0; rep < 2 && rc == CQ_OK; ++rep) {
+        // a warm-up build, then the faster of two profiled builds per class
+        for (int rep = 0; rep < 3 && rc == CQ_OK; ++rep) {
             cq_fock_stats st;
-            rc = cq_fock_build(b, kind, P, J, K, &o, &st, stream);
+            if ((rc = cq_fock_build(b, kind, P, J, K, &o, &st, stream))) break;
+            if (rep == 0) continue;
+            for (int q = 0; q < NQC && rc == CQ_OK; ++q)
+                for (int p = p0; p < np; ++p) {
+                    if (!allowed(q, p, v)) continue;
+                    double ms = 0.0;
+                    unsigned long long nq = 0, npr = 0;
+                    if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &npr))) break;
+                    t[q][p][v] = std::min(t[q][p][v], ms);
+                }
         }
-        if (rc) break;
-        for (int q = 0; q < NQC; ++q)
-            for (int p = 0; p < np; ++p) {
-                if (!allowed(q, p, v)) continue;
-                double ms = 0.0;
-                unsigned long long nq = 0, npr = 0;
-                if ((rc = cq_fock_class_stats(b, q, p, &ms, &nq, &npr))) break;
-                t[q][p][v] = ms;
-            }
     }
     b->profile = old_profile;
     if (rc) {
@@ -745,7 +763,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     }
     int best[NQC][3], second[NQC][3];
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < np; ++p) {
+        for (int p = p0; p < np; ++p) {
             best[q][p] = DEFAULT_VARIANT[q][p];
             second[q][p] = -1;
             for (int v = 0; v < NVARIANT; ++v)
@@ -775,7 +793,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     };
     std::vector<std::pair<double, int>> cand;
     for (int q = 0; q < NQC; ++q)
-        for (int p = 0; p < np; ++p)
+        for (int p = p0; p < np; ++p)
             if (second[q][p] >= 0) cand.push_back({t[q][p][best[q][p]], 3 * q + p});
     std::sort(cand.begin(), cand.end(), [](const std::pair<double, int>& x, const std::pair<double, int>& y) {
         return x.first > y.first;
@@ -802,7 +820,7 @@ extern "C" int cq_autotune(cq_basis* b, int kind, const void* P, const cq_fock_o
     if (rc) return rc;
     for (int q = 0; q < NQC; ++q)
         for (int p = 0; p < 3; ++p) {
-            const double ms = p < np ? t[q][p][best[q][p]] : 1e300;
+            const double ms = (p >= p0 && p < np) ? t[q][p][best[q][p]] : 1e300;
             if (table) table[3 * q + p] = b->variant[q][p];
             if (ms_out) ms_out[3 * q + p] = ms < 1e299 ? ms : 0.0;
         }

@@ -143,6 +143,10 @@ struct cq_basis {
     std::vector<void*> dense_bufs; // other driver scratch, freed with the basis
     void* rt = nullptr;            // RT-TDHF buffers (cq_drivers.cu)
     int variant[cq::NQC][3] = {};  // kernel variant per class and precision (FP64, FP32, double-float)
+    // cooperative kernel on the screened list, per precision: warp tasks per
+    // quartet (at most) and primitive quartets per task (about)
+    int list_split[3] = {8, 4, 4};
+    int list_chunk[3] = {64, 32, 32};
     // tasks of the warp-cooperative kernel: (bra, ket, primitive range), built
     // for the classes that use it, rebuilt when the variant table changes
     std::vector<int> coop_off;     // NQC + 1

@@ -45,12 +45,9 @@ struct JKArgs {
     const int* mol_mode;          // optional per-molecule mode (see ClassifyArgs), read by the
     long long lds2;               // cooperative kernel, which screens its own tasks
     int coop_list;                // cooperative kernel: 1 = quartets from qlist (already screened)
-    int tier3;                    // build with a double-float tier (the FP64 lists hold only the
-                                  // largest bounds: short lists of deep quartets)
-    int grid_cap;                 // largest grid (CTAs) of this launch; 0: jk_grid_cap().  The
-                                  // kernels stride over their list, so any grid is correct; short
-                                  // lists get small grids that leave the SMs to the concurrent
-                                  // class kernels of the other streams
+    int fp64_tier;                // the FP64 list of a three-tier build (short, deep quartets)
+    int coop_split;               // cooperative kernel, list mode: warp tasks per quartet, at most
+    int coop_chunk;               // ... and primitive quartets per task, about
 };
 
 template <typename R>

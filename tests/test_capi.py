@@ -86,6 +86,7 @@ def test_every_entry_point_rejects_null_arguments(libcq):
         "cq_fock_class_stats": (None, c_int(0), c_int(0), None, None, None),
         "cq_fock_set_variant": (None, c_int(0), c_int(0), c_int(0)),
         "cq_fock_get_variant": (None, c_int(0), c_int(0), None),
+        "cq_fock_set_list_split": (None, c_int(0), c_int(1), c_int(1)),
         "cq_autotune": (None, c_int(0), None, None, None, None, None),
         "cq_one_electron": (None, None, None, None, None, None, None),
         "cq_scf": (None, c_int(1), None, None, None, None, None, None),
