@@ -33,9 +33,17 @@ LANES = {"2222": 32, "2221": 8, "2220": 4, "2211": 4, "2121": 4,
 
 # classes without an axis-permutation kernel: their double-float tier runs
 # the lane-group kernel, DF_LANES lanes per quartet (the double-float lists
-# are short and their quartets deep: about 150 primitive quartets each)
+# are short and their quartets deep: about 150 primitive quartets each;
+# 8 lanes beat 4 and 2 on the 16-atom workload)
 LANE_DF = ("0000", "1000", "1010", "1100", "1110", "2000", "2010", "2100")
-DF_LANES = 4
+DF_LANES = 8
+
+# FP32 lane groups where they differ from LANES: the fastest of 1, 2, 4, 8
+# per class on the 16-atom workload's FP32 lists (splitting a quartet's
+# primitive quartets over lanes coalesces their loads and evens out the
+# work of a warp; larger groups pay in reduction shuffles)
+F32_LANES = {"0000": 8, "1000": 4, "1010": 4, "1100": 4, "1110": 2, "2000": 4, "2010": 2, "2011": 2,
+             "2020": 2, "2100": 4, "2110": 2, "2200": 8, "1111": 4}
 
 # axis-permutation kernels: lanes per frame splitting the primitive quartets
 # (FP64 lists are the short, large-bound part of a mixed build)
@@ -87,7 +95,8 @@ def gen_sources():
         if cls in LANE_DF:
             precs.append(("df", "df"))
         for R, tag in precs:
-            G = DF_LANES if tag == "df" else LANES.get(cls, 1)
+            G = DF_LANES if tag == "df" else F32_LANES.get(cls, LANES.get(cls, 1)) if tag == "f32" \
+                else LANES.get(cls, 1)
             src = head + [
                 f"void launch_jk_{cls}_{tag}(const JKArgs& a, cudaStream_t s)",
                 "{",
