@@ -165,7 +165,7 @@ def gen_sources():
             f"static void launch_sym_{cls}_t(const JKArgs& a, cudaStream_t s)",
             "{",
             f"    constexpr int qc = {qc_of[cls]}, G = {G}, NGRP = 32 / (G * H), WARPS = SYM_THREADS / 32;",
-            "    const int nslots = COOP_SIZES[qc].nslots;",
+            "    const int nslots = COOP_SIZES[qc].hslots;",
             "    const size_t bytes = (size_t)WARPS * sym_warp_bytes<R>(nslots);",
             f"    auto kern = jk_sym_kernel<{la}, {lb}, {lc}, {ld}, R, G, H>;",
             "    static int attr_done = 0;",

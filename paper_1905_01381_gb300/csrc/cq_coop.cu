@@ -11,8 +11,8 @@ template <typename R>
 static void launch_coop_t(const JKArgs& a, int qc, cudaStream_t s)
 {
     static int attr_done = 0;
-    const int nslots = COOP_SIZES[qc].nslots;
-    const size_t bytes = (size_t)COOP_WARPS * coop_warp_bytes<R>(nslots);
+    const int wslots = coop_region_slots(COOP_SIZES[qc].vslots, COOP_SIZES[qc].hslots);
+    const size_t bytes = (size_t)COOP_WARPS * coop_warp_bytes<R>(wslots);
     if (!attr_done) {
         cudaFuncSetAttribute(jk_coop_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         attr_done = 1;
@@ -22,7 +22,7 @@ static void launch_coop_t(const JKArgs& a, int qc, cudaStream_t s)
     if (blocks == 0) return;
     const long long cap = jk_grid_cap();
     if (a.coop_list && blocks > cap) blocks = cap;   // warps stride over the list
-    jk_coop_kernel<R><<<(unsigned)blocks, COOP_THREADS, bytes, s>>>(a, qc, nslots);
+    jk_coop_kernel<R><<<(unsigned)blocks, COOP_THREADS, bytes, s>>>(a, qc, wslots);
 }
 
 // prec: 0 FP64, 1 FP32, 2 double-float
@@ -35,8 +35,8 @@ void launch_coop(const JKArgs& a, int qc, int prec, cudaStream_t s)
 
 size_t coop_smem_bytes(int qc, int prec)
 {
-    const int nslots = COOP_SIZES[qc].nslots;
-    return (size_t)COOP_WARPS * (prec == 1 ? coop_warp_bytes<float>(nslots) : coop_warp_bytes<double>(nslots));
+    const int wslots = coop_region_slots(COOP_SIZES[qc].vslots, COOP_SIZES[qc].hslots);
+    return (size_t)COOP_WARPS * (prec == 1 ? coop_warp_bytes<float>(wslots) : coop_warp_bytes<double>(wslots));
 }
 
 }  // namespace cq

@@ -35,12 +35,24 @@ struct CoopClass {
 // per-class slot counts for shared-memory sizing on the host
 struct CoopSize {
     int nslots, nacc, N;
+    int vslots, hslots;   // slots of the vertical and of the horizontal recurrence
 };
 
-template <typename R>
-__host__ __device__ constexpr size_t coop_warp_bytes(int nslots)
+// Slots of a warp's region in the cooperative kernel: the coefficient and
+// Boys buffers (32 primitive quartets) followed by the vertical recurrence's
+// slots; the horizontal recurrence and the digestion, which need neither
+// buffer, reuse the whole region.
+constexpr int COOP_BUF_SLOTS = 32 * COOP_NCOEF + 32 * (LTOT_MAX + 1);
+__host__ __device__ constexpr int coop_region_slots(int vslots, int hslots)
 {
-    return (size_t)(32 * COOP_NCOEF + 32 * (LTOT_MAX + 1) + nslots + 6 * 36 + 8) * sizeof(R) + 64 * sizeof(int);
+    return COOP_BUF_SLOTS + vslots > hslots ? COOP_BUF_SLOTS + vslots : hslots;
+}
+
+// bytes of a warp: region, density blocks, AB and CD
+template <typename R>
+__host__ __device__ constexpr size_t coop_warp_bytes(int region_slots)
+{
+    return (size_t)(region_slots + 6 * 36 + 8) * sizeof(R);
 }
 
 }  // namespace cq

@@ -174,11 +174,13 @@ __device__ __forceinline__ bool coop_selected(const JKArgs& a, const PairHdr& B,
 // One task: primitive quartets [p0, p1) of quartet (ib, j), their vertical
 // recurrences, the contraction, HRR and digestion.  HRR and digestion are
 // linear, so a chunk of primitive quartets is digested on its own and the
-// J'/K' adds of all chunks sum to the quartet's.
+// J'/K' adds of all chunks sum to the quartet's.  coef, Sb and V lie one
+// after the other in the warp's region, which the HRR and the digestion
+// reuse from coef on once the vertical recurrences are done.
 template <typename R>
 __device__ __forceinline__ void coop_task(const JKArgs& a, const CoopClass& C, int ib, int j, int p0, int p1,
-                                          const PairHdr& B, const PairHdr& K, R* __restrict__ coef,
-                                          R* __restrict__ Sb, R* __restrict__ V, R* __restrict__ Db,
+                                          const PairHdr& B, const PairHdr& K, R* coef,
+                                          R* Sb, R* V, R* __restrict__ Db,
                                           R* __restrict__ hc, int lane, unsigned long long& nq,
                                           unsigned long long& np)
 {
@@ -256,22 +258,22 @@ __device__ __forceinline__ void coop_task(const JKArgs& a, const CoopClass& C, i
 #pragma unroll
     for (int k = 0; k < COOP_MAXACC; ++k) {
         const int tt = lane + 32 * k;
-        if (tt < C.nacc) V[C.N + tt] = acc[k];
+        if (tt < C.nacc) coef[C.N + tt] = acc[k];
     }
-    coop_hrr_digest<R>(C, V, Db, hc, B, K, ib, j, a, lane);
+    coop_hrr_digest<R>(C, coef, Db, hc, B, K, ib, j, a, lane);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_kernel(const JKArgs a, int qc, int nslots_max)
+__global__ void __launch_bounds__(COOP_THREADS, CoopMinBlocks<R>::v) jk_coop_kernel(const JKArgs a, int qc, int wslots)
 {
     const CoopClass C = COOP_CLASSES_D[qc];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char* wbase = smem_raw + (size_t)wib * coop_warp_bytes<R>(nslots_max);
-    R* coef = (R*)wbase;                                   // [32][NCOEF]
+    unsigned char* wbase = smem_raw + (size_t)wib * coop_warp_bytes<R>(wslots);
+    R* coef = (R*)wbase;                                   // [32][NCOEF]; the HRR region from here
     R* Sb = coef + 32 * COOP_NCOEF;                        // [32][LTOT_MAX+1]
-    R* V = Sb + 32 * (LTOT_MAX + 1);                       // [nslots]
-    R* Db = V + nslots_max;                                // 6 density blocks of <= 36
+    R* V = Sb + 32 * (LTOT_MAX + 1);                       // VRR slots
+    R* Db = coef + wslots;                                 // 6 density blocks of <= 36
     R* hc = Db + 6 * 36;                                   // AB, CD
     unsigned long long nq = 0, np = 0;
     if (a.coop_list) {

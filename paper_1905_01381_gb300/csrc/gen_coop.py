@@ -327,12 +327,14 @@ def emit(outdir, classes):
             f"{{{la}, {lb}, {lc}, {ld}, {v['L']}, {v['nacc']}, {h['N']}, {nslots}, "
             f"{len(v['groups'])}, {len(h['groups'])}, g_vgrp_{cls}, g_vdesc_{cls}, g_hgrp_{cls}, g_hdesc_{cls}, g_tgt_{cls}}}")
         stats[cls] = dict(vrr_nodes=v["nodes"], vrr_groups=len(v["groups"]), vrr_flops=v["flops"],
-                          hrr_flops=h["flops"], nslots=nslots, nacc=v["nacc"], N=h["N"])
+                          hrr_flops=h["flops"], nslots=nslots, nacc=v["nacc"], N=h["N"],
+                          vslots=v["nslots"], hslots=h["nslots"])
     lines.append("__device__ const CoopClass COOP_CLASSES_D[NQC_COOP] = {")
     lines.append(",\n".join(dir_entries))
     lines.append("};")
     lines.append("const CoopSize COOP_SIZES[NQC_COOP] = {")
-    lines.append(",\n".join(f"{{{st['nslots']}, {st['nacc']}, {st['N']}}}" for st in stats.values()))
+    lines.append(",\n".join(f"{{{st['nslots']}, {st['nacc']}, {st['N']}, {st['vslots']}, {st['hslots']}}}"
+                            for st in stats.values()))
     lines.append("};")
     lines.append("}  // namespace cq")
     return "\n".join(lines) + "\n", stats
