@@ -334,15 +334,16 @@ def cpu_baseline(seconds: float, ref_frac: float):
 
 # ---------------------------------------------------------------- GPU arm
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic_jk_rt16.json")
-KERNEL_SOURCES = ("cq_common.cuh", "cq_df.cuh", "cq_jk.cuh", "cq_coop.cuh", "cq_coop_kernel.cuh", "cq_sym.cuh",
-                  "gen_eri.py", "gen_coop.py", "gen_sym.py")
+KERNEL_SOURCES = ("csrc/cq_common.cuh", "csrc/cq_df.cuh", "csrc/cq_jk.cuh", "csrc/cq_coop.cuh",
+                  "csrc/cq_coop_kernel.cuh", "csrc/cq_sym.cuh", "csrc/gen_eri.py", "csrc/gen_coop.py",
+                  "csrc/gen_sym.py", "buildlib.py")   # buildlib.py: lanes per quartet of each kernel
 
 
 def kernel_sources_sha1():
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_1905_01381_gb300", "csrc", f), "rb").read())
+        h.update(open(os.path.join(ROOT, "paper_1905_01381_gb300", f), "rb").read())
     return h.hexdigest()
 
 
