@@ -566,7 +566,7 @@ def _driver_setup():
 def _line(metric, value, unit, hib, args, ms, config, extra, clk, launches):
     out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": hib, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic", "config": config,
+           "vs_baseline": None, "dtype": "f64+df+f32", "data": "synthetic", "config": config,
            "gpu_launches": launches, "clocks": clk.summary()}
     out.update(extra)
     print(json.dumps(out))
@@ -670,11 +670,14 @@ def run_scf(args):
     b = cq.Basis(mol, bas)
     nocc = mol.n_electrons() // 2
     P = torch.as_tensor(synth.density(b.nbf, nocc, 5), device="cuda")
-    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, cache=False)
+    # FP64 kernels for the all-FP64 run and builds; FP32 and double-float for the mixed ones
+    b.autotune(P, prec=cq.CQ_PREC_FP64, cache=False)
+    b.autotune(P, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, cache=False)
     for _ in range(args.warmup):
         b.fock_build(P)
     modes = {"fp64": dict(prec=cq.CQ_PREC_FP64),
-             "mixed": dict(prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, incremental=True, switch_tol=1e-5)}
+             "mixed": dict(prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, incremental=True,
+                           switch_tol=1e-5)}
     res = {}
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         for name, kw in modes.items():
@@ -686,13 +689,14 @@ def run_scf(args):
                 torch.cuda.synchronize()
                 ts.append(time.perf_counter() - t0)
             res[name] = {"s": statistics.median(ts), "energy": st["energy"], "iterations": st["iterations"],
-                         "quartets_fp64": st["quartets_fp64"], "quartets_fp32": st["quartets_fp32"]}
+                         "quartets_fp64": st["quartets_fp64"], "quartets_fp32": st["quartets_fp32"],
+                         "quartets_df": st["quartets_df"]}
     dE = abs(res["mixed"]["energy"] - res["fp64"]["energy"])
     b.close()
     _line("RHF SCF time to converged energy (mixed + incremental vs FP64)", res["mixed"]["s"], "s", False, args,
           res["mixed"]["s"] * 1e3,
           {"workload": WORKLOAD.replace("complex-Hermitian P (29 occ)", "RHF, 29 doubly occupied"),
-           "e_tol": 1e-10, "d_tol": 1e-8, "mixed_tol": MIXED_TOL, "switch_tol": 1e-5},
+           "e_tol": 1e-10, "d_tol": 1e-8, "mixed_tol": MIXED_TOL, "fp64_tol": FP64_TOL, "switch_tol": 1e-5},
           {"fp64_s": res["fp64"]["s"], "speedup_vs_fp64": res["fp64"]["s"] / res["mixed"]["s"],
            "dE_mixed_vs_fp64_Eh": dE, "runs": res}, clk, None)
     return 0
@@ -710,13 +714,14 @@ def run_rt(args):
     nocc = mol.n_electrons() // 2
     D, _, st = b.scf(nocc, d_tol=1e-10)
     P0 = D.to(torch.complex128)
-    b.autotune(P0, prec=cq.CQ_PREC_MIXED, mixed_tol=RT_MIXED_TOL, cache=False)
+    b.autotune(P0, prec=cq.CQ_PREC_FP64, cache=False)
+    b.autotune(P0, prec=cq.CQ_PREC_MIXED, mixed_tol=RT_MIXED_TOL, fp64_tol=FP64_TOL, cache=False)
     dt = 0.05
     field = dict(field=(0.0, 0.0, 1e-4), t_on=0.0, t_off=dt)
     traces, rates = {}, {}
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
         for name, kw in (("fp64", dict(prec=cq.CQ_PREC_FP64)),
-                         ("mixed", dict(prec=cq.CQ_PREC_MIXED, mixed_tol=RT_MIXED_TOL))):
+                         ("mixed", dict(prec=cq.CQ_PREC_MIXED, mixed_tol=RT_MIXED_TOL, fp64_tol=FP64_TOL))):
             Pp, Pc = P0.clone(), P0.clone()
             for k in range(args.warmup):
                 b.rt_step(k, Pp, Pc, dt=dt, **field, **kw)
@@ -736,7 +741,7 @@ def run_rt(args):
     _line("RT-TDHF MMUT/EM2 steps/s (mixed vs FP64)", rates["mixed"], "steps/s", True, args,
           1e3 / rates["mixed"],
           {"workload": WORKLOAD.replace("complex-Hermitian P (29 occ)", "RHF ground state, delta kick 1e-4 au z"),
-           "dt": dt, "steps": args.rt_steps, "restart_every": 50, "mixed_tol": RT_MIXED_TOL},
+           "dt": dt, "steps": args.rt_steps, "restart_every": 50, "mixed_tol": RT_MIXED_TOL, "fp64_tol": FP64_TOL},
           {"fp64_steps_per_s": rates["fp64"],
            "max_abs_dmu_z_mixed_vs_fp64": float(np.abs(mu["mixed"] - mu["fp64"]).max()),
            "mu_z_response_range": float(np.ptp(mu["fp64"])),

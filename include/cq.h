@@ -312,6 +312,8 @@ typedef struct {
     int guess_fallback;  /* cq_scf_batch with D_in: a molecule still open at this
                             iteration (> 1) restarts from the core guess with a
                             fresh DIIS subspace; 0 = never */
+    double fp64_tol;     /* mixed builds: double-float tier for mixed_tol <= bound
+                            < fp64_tol, as in cq_fock_opts; 0 = two tiers */
 } cq_scf_opts;
 typedef struct {
     double energy;
@@ -321,6 +323,7 @@ typedef struct {
     double ms;
     int graph;           /* cq_scf_batch: 2 whole iteration replayed as a graph,
                             1 graphs around an eager eigensolver call, 0 eager */
+    unsigned long long quartets_df;  /* double-float quartets, summed over iterations */
 } cq_scf_stats;
 int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const double* D_in,
            double* D_out, double* F_out, cq_scf_stats* stats, void* stream);
@@ -393,6 +396,7 @@ typedef struct {
     int prec;            /* cq_prec */
     double mixed_tol;
     double schwarz_tol;
+    double fp64_tol;     /* mixed builds: double-float tier below it (cq_fock_opts); 0 = two tiers */
 } cq_rt_opts;
 typedef struct {
     double dipole[3];

@@ -41,19 +41,21 @@ class SCFOpts(ctypes.Structure):
     _fields_ = [("e_tol", ctypes.c_double), ("d_tol", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("diis_size", ctypes.c_int), ("prec", ctypes.c_int), ("mixed_tol", ctypes.c_double),
                 ("schwarz_tol", ctypes.c_double), ("incremental", ctypes.c_int), ("full_every", ctypes.c_int),
-                ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int), ("guess_fallback", ctypes.c_int)]
+                ("switch_tol", ctypes.c_double), ("graph", ctypes.c_int), ("guess_fallback", ctypes.c_int),
+                ("fp64_tol", ctypes.c_double)]
 
 
 class SCFStats(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("iterations", ctypes.c_int), ("converged", ctypes.c_int),
                 ("last_rms", ctypes.c_double), ("quartets_fp64", ctypes.c_ulonglong),
-                ("quartets_fp32", ctypes.c_ulonglong), ("ms", ctypes.c_double), ("graph", ctypes.c_int)]
+                ("quartets_fp32", ctypes.c_ulonglong), ("ms", ctypes.c_double), ("graph", ctypes.c_int),
+                ("quartets_df", ctypes.c_ulonglong)]
 
 
 class RTOpts(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_double), ("field", ctypes.c_double * 3), ("t_on", ctypes.c_double),
                 ("t_off", ctypes.c_double), ("restart_every", ctypes.c_int), ("prec", ctypes.c_int),
-                ("mixed_tol", ctypes.c_double), ("schwarz_tol", ctypes.c_double)]
+                ("mixed_tol", ctypes.c_double), ("schwarz_tol", ctypes.c_double), ("fp64_tol", ctypes.c_double)]
 
 
 class RTObs(ctypes.Structure):
@@ -236,7 +238,7 @@ class Basis:
 
     def scf_batch(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
                   mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, D0=None, stream=None,
-                  raise_on_fail=True, graph=True, guess_fallback=40):
+                  raise_on_fail=True, graph=True, guess_fallback=40, fp64_tol=0.0):
         """Batched RHF; returns (D batched tensor, energies, iterations, stats).
         With D0, a molecule still open after guess_fallback iterations restarts
         from the core guess (0: never)."""
@@ -246,7 +248,7 @@ class Basis:
         E = np.zeros(self.nmol)
         it = np.zeros(self.nmol, dtype=np.int32)
         o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, int(bool(graph)),
-                    int(guess_fallback))
+                    int(guess_fallback), fp64_tol)
         st = SCFStats()
         ip, dp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
         rc = lib().cq_scf_batch(self.h, no.ctypes.data_as(ip), ctypes.byref(o),
@@ -255,8 +257,8 @@ class Basis:
         if raise_on_fail:
             check(rc, "cq_scf_batch")
         return D, E, it, {"iterations": st.iterations, "converged": st.converged, "ms": st.ms,
-                          "quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32, "rc": rc,
-                          "graph": st.graph}
+                          "quartets_fp64": st.quartets_fp64, "quartets_fp32": st.quartets_fp32,
+                          "quartets_df": st.quartets_df, "rc": rc, "graph": st.graph}
 
     def close(self):
         if getattr(self, "h", None):
@@ -369,14 +371,15 @@ class Basis:
 
     def scf(self, nocc, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
             mixed_tol=1e-5, schwarz_tol=1e-14, incremental=False, full_every=8, switch_tol=1e-5,
-            D0=None, stream=None, raise_on_fail=True):
-        """RHF SCF; returns (D, F, stats dict)."""
+            D0=None, stream=None, raise_on_fail=True, fp64_tol=0.0):
+        """RHF SCF; returns (D, F, stats dict).  fp64_tol > mixed_tol adds the
+        double-float tier to the mixed builds."""
         import torch
         n = self.nbf
         D = torch.empty((n, n), dtype=torch.float64, device="cuda")
         F = torch.empty((n, n), dtype=torch.float64, device="cuda")
         o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, int(incremental),
-                    full_every, switch_tol)
+                    full_every, switch_tol, 0, 0, fp64_tol)
         st = SCFStats()
         rc = lib().cq_scf(self.h, int(nocc), ctypes.byref(o), _ptr(D0) if D0 is not None else None,
                           _ptr(D), _ptr(F), ctypes.byref(st), _stream_ptr(stream))
@@ -384,18 +387,19 @@ class Basis:
             check(rc, "cq_scf")
         stats = {"energy": st.energy, "iterations": st.iterations, "converged": bool(st.converged),
                  "last_rms": st.last_rms, "quartets_fp64": st.quartets_fp64,
-                 "quartets_fp32": st.quartets_fp32, "ms": st.ms, "rc": rc}
+                 "quartets_fp32": st.quartets_fp32, "quartets_df": st.quartets_df, "ms": st.ms, "rc": rc}
         return D, F, stats
 
     def scf_ghf(self, nelec, e_tol=1e-10, d_tol=1e-8, max_iter=128, diis_size=8, prec=CQ_PREC_FP64,
-                mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, P0=None, stream=None, raise_on_fail=True):
+                mixed_tol=1e-5, schwarz_tol=1e-14, switch_tol=1e-5, P0=None, stream=None, raise_on_fail=True,
+                fp64_tol=0.0):
         """Two-component GHF SCF; P0 and the returned P, F are (4, nbf, nbf)
         complex128 Pauli components.  Returns (P, F, stats dict)."""
         import torch
         n = self.nbf
         P = torch.empty((4, n, n), dtype=torch.complex128, device="cuda")
         F = torch.empty((4, n, n), dtype=torch.complex128, device="cuda")
-        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, 0, 0)
+        o = SCFOpts(e_tol, d_tol, max_iter, diis_size, prec, mixed_tol, schwarz_tol, 0, 8, switch_tol, 0, 0, fp64_tol)
         st = SCFStats()
         rc = lib().cq_scf_ghf(self.h, int(nelec), ctypes.byref(o),
                               _ptr(P0.contiguous()) if P0 is not None else None, _ptr(P), _ptr(F),
@@ -404,16 +408,16 @@ class Basis:
             check(rc, "cq_scf_ghf")
         stats = {"energy": st.energy, "iterations": st.iterations, "converged": bool(st.converged),
                  "last_rms": st.last_rms, "quartets_fp64": st.quartets_fp64,
-                 "quartets_fp32": st.quartets_fp32, "ms": st.ms, "rc": rc}
+                 "quartets_fp32": st.quartets_fp32, "quartets_df": st.quartets_df, "ms": st.ms, "rc": rc}
         return P, F, stats
 
     def rt_step(self, step, P_prev, P_cur, dt=0.05, field=(0.0, 0.0, 0.0), t_on=0.0, t_off=0.0,
                 restart_every=50, prec=CQ_PREC_FP64, mixed_tol=1e-5, schwarz_tol=1e-14, obs=True,
-                stream=None):
+                stream=None, fp64_tol=0.0):
         """One MMUT/EM2 step; P_prev, P_cur complex128 (nbf, nbf) CUDA tensors updated in
         place.  Returns the observables of the density on entry (dict) or None."""
         o = RTOpts(dt, (ctypes.c_double * 3)(*field), t_on, t_off, restart_every, prec, mixed_tol,
-                   schwarz_tol)
+                   schwarz_tol, fp64_tol)
         ob = RTObs()
         check(lib().cq_rt_step(self.h, ctypes.byref(o), int(step), _ptr(P_prev), _ptr(P_cur),
                                ctypes.byref(ob) if obs else None, _stream_ptr(stream)), "cq_rt_step")

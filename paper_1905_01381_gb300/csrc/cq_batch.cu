@@ -435,7 +435,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
                             double* E_out, int* iters_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !nocc || !D_out) { set_error("cq_scf_batch: NULL argument"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 1, 0};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 1, 0, 0.0};
     if (opts) o = *opts;
     // the core-guess fallback applies to a supplied starting density only
     const int restart_iter = (D_in && o.guess_fallback > 1) ? o.guess_fallback : 0;
@@ -530,7 +530,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     GETB(Fc, ms) GETB(Dc, ms) GETB(Sc, ms) GETB(Xc, ms) GETB(shc, (size_t)nmol * ld) GETB(T1, ms) GETB(T2, ms)
     GETB(Epc, ms) GETB(Fdc, ms) GETB(Dnc, ms) GETB(w, (size_t)nmol * ld)
     for (int k = 0; k < ds; ++k) { GETB(Fs.p[k], ms) GETB(Es.p[k], ms) }
-    GETB(conv, nmol) GETB(iters, nmol) GETB(d_nocc, nmol) GETB(info, nmol) GETB(mode, nmol) GETB(acc, 4)
+    GETB(conv, nmol) GETB(iters, nmol) GETB(d_nocc, nmol) GETB(info, nmol) GETB(mode, nmol) GETB(acc, 6)
     GETB(bst, 1) GETB(kdm, nmol) GETB(restart, nmol) GETB(act, nmol) GETB(nocc_c, nmol)
     if (restart_iter) GETB(Dcore, ms)
 #undef GETB
@@ -598,7 +598,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     };
     if (cudaMemsetAsync(conv, 0, nmol * sizeof(int), s) || cudaMemsetAsync(iters, 0, nmol * sizeof(int), s) ||
         cudaMemsetAsync(Eold, 0, nmol * sizeof(double), s) || cudaMemsetAsync(E, 0, nmol * sizeof(double), s) ||
-        cudaMemsetAsync(acc, 0, 4 * sizeof(unsigned long long), s) || cudaMemsetAsync(bst, 0, sizeof(BatchState), s) ||
+        cudaMemsetAsync(acc, 0, 6 * sizeof(unsigned long long), s) || cudaMemsetAsync(bst, 0, sizeof(BatchState), s) ||
         cudaMemsetAsync(kdm, 0, nmol * sizeof(int), s) || cudaMemsetAsync(restart, 0, nmol * sizeof(int), s))
         return fail(CQ_ERR_CUDA);
     const int mode0 = o.prec == CQ_PREC_MIXED ? MODE_FP32 : 0;
@@ -629,7 +629,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     // the eigensolver, then phase B (density, written back per molecule).
     auto phase_a = [&](int kb, bool first) -> int {
         batch_begin_kernel<<<1, 1024, 0, s>>>(nmol, kb, conv, d_nocc, bst, act, nocc_c);
-        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, o.prec, 1, 1};
+        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, o.prec, 1, 1, o.fp64_tol};
         int r = fock_build_modes(b, CQ_DENS_REAL_SYM, D, J, K, &fo, nullptr, s, mode, acc);
         if (r) return r;
         batch_fock_kernel<<<nb256(ms), 256, 0, s>>>(ms, H, J, K, F);
@@ -753,7 +753,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     if (cudaMemcpyAsync(D_out, D, ms * sizeof(double), cudaMemcpyDeviceToDevice, s)) return fail(CQ_ERR_CUDA);
     std::vector<double> hE(nmol);
     std::vector<int> hit(nmol), hconv(nmol);
-    unsigned long long hacc[4];
+    unsigned long long hacc[6];
     if (cudaMemcpyAsync(hE.data(), E, nmol * sizeof(double), cudaMemcpyDeviceToHost, s) ||
         cudaMemcpyAsync(hit.data(), iters, nmol * sizeof(int), cudaMemcpyDeviceToHost, s) ||
         cudaMemcpyAsync(hconv.data(), conv, nmol * sizeof(int), cudaMemcpyDeviceToHost, s) ||
@@ -776,6 +776,7 @@ extern "C" int cq_scf_batch(cq_basis* b, const int* nocc, const cq_scf_opts* opt
     st.converged = nconv;
     st.quartets_fp64 = hacc[0];
     st.quartets_fp32 = hacc[2];
+    st.quartets_df = hacc[4];
     st.ms = msf;
     st.graph = o.graph && !b->profile ? graph_level : 0;
     if (stats) *stats = st;

@@ -351,7 +351,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
                       double* F_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !D_out) { set_error("cq_scf: NULL basis or output"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0, 0.0};
     if (opts) o = *opts;
     const int n = b->nbf;
     if (b->nmol > 1) { set_error("cq_scf: batched basis; use cq_scf_batch"); return CQ_ERR_UNSUPPORTED; }
@@ -428,7 +428,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
     int it = 0;
     for (it = 1; it <= o.max_iter; ++it) {
         const bool incremental = o.incremental && since_full > 0 && since_full < o.full_every;
-        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, final_fp64 ? CQ_PREC_FP64 : CQ_PREC_MIXED, 1, 1};
+        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, final_fp64 ? CQ_PREC_FP64 : CQ_PREC_MIXED, 1, 1, o.fp64_tol};
         cq_fock_stats fst;
         const double* Dbuild = D;
         if (incremental) {
@@ -439,6 +439,7 @@ extern "C" int cq_scf(cq_basis* b, int nocc, const cq_scf_opts* opts, const doub
         if (rc) { cleanup(); return rc; }
         st.quartets_fp64 += fst.quartets_fp64;
         st.quartets_fp32 += fst.quartets_fp32;
+        st.quartets_df += fst.quartets_df;
         since_full = incremental ? since_full + 1 : 1;
         fock_real_kernel<<<nblk(nn), 256, 0, s>>>(nn, incremental ? 1 : 0, b->d_H, J, K, G, F);
         rhf_energy_kernel<<<1, 256, 0, s>>>(nn, b->d_H, F, D, b->enuc, scal);
@@ -599,7 +600,7 @@ static int fock_ortho(cq_basis* b, RTBufs& r, const cq_rt_opts& o, const cuDoubl
 {
     int rc = to_ao(b, r, Pp, r.Pao);
     if (rc) return rc;
-    cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, o.prec, 1, 1};
+    cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, o.prec, 1, 1, o.fp64_tol};
     rc = cq_fock_build(b, CQ_DENS_COMPLEX_HERM, r.Pao, r.J, r.K, &fo, nullptr, s);
     if (rc) return rc;
     const bool on = t >= o.t_on && t < o.t_off;
@@ -815,7 +816,7 @@ extern "C" int cq_scf_ghf(cq_basis* b, int nelec, const cq_scf_opts* opts, const
                           void* F_out, cq_scf_stats* stats, void* stream)
 {
     if (!b || !P_out) { set_error("cq_scf_ghf: NULL basis or output"); return CQ_ERR_INVALID_ARG; }
-    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0};
+    cq_scf_opts o{1e-10, 1e-8, 128, 8, CQ_PREC_FP64, 1e-5, 1e-14, 0, 8, 1e-5, 0, 0, 0.0};
     if (opts) o = *opts;
     const int n = b->nbf;
     if (b->nmol > 1) { set_error("cq_scf_ghf: batched basis"); return CQ_ERR_UNSUPPORTED; }
@@ -909,11 +910,12 @@ extern "C" int cq_scf_ghf(cq_basis* b, int nelec, const cq_scf_opts* opts, const
     int nvec = 0, head = 0, it = 0;
     bool final_fp64 = (o.prec == CQ_PREC_FP64), converged = false;
     for (it = 1; it <= o.max_iter; ++it) {
-        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, final_fp64 ? CQ_PREC_FP64 : CQ_PREC_MIXED, 1, 1};
+        cq_fock_opts fo{o.schwarz_tol, o.mixed_tol, final_fp64 ? CQ_PREC_FP64 : CQ_PREC_MIXED, 1, 1, o.fp64_tol};
         cq_fock_stats fst;
         if ((rc = cq_fock_build(b, CQ_DENS_PAULI4, P, J, K, &fo, &fst, s))) { cleanup(); return rc; }
         st.quartets_fp64 += fst.quartets_fp64;
         st.quartets_fp32 += fst.quartets_fp32;
+        st.quartets_df += fst.quartets_df;
         ghf_fock_kernel<<<nblk(nn), 256, 0, s>>>(nn, b->d_H, J, K, F);
         ghf_hf_kernel<<<nblk(4 * nn), 256, 0, s>>>(nn, b->d_H, F, HF);
         // Re sum (h^I + F^I)_ij conj(P^I_ij) = Re Tr[(h^I + F^I) P^I] for Hermitian P^I

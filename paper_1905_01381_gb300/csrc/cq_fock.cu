@@ -566,12 +566,12 @@ extern "C" int cq_fock_get_variant(const cq_basis* b, int qc, int prec, int* var
     return CQ_OK;
 }
 
-// Adds the four totals (FP64 quartets, FP64 primitive quartets, FP32
-// quartets, FP32 primitive quartets) of a build into a running accumulator.
+// Adds the six totals (quartets and primitive quartets in FP64, FP32 and
+// double-float) of a build into a running accumulator.
 namespace cq {
 __global__ void counter_accumulate_kernel(const unsigned long long* __restrict__ c, unsigned long long* __restrict__ acc)
 {
-    if (threadIdx.x < 4) acc[threadIdx.x] += c[threadIdx.x];
+    if (threadIdx.x < 6) acc[threadIdx.x] += c[threadIdx.x];
 }
 }  // namespace cq
 

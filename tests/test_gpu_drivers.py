@@ -66,14 +66,19 @@ def test_rhf_energy_matches_oracle(cq, dr, case):
     assert abs(np.trace(Dg @ S) - nocc) < 1e-10
 
 
-def test_rhf_mixed_incremental_same_energy(cq):
+@pytest.mark.parametrize("fp64_tol", [0.0, 1e-2])
+def test_rhf_mixed_incremental_same_energy(cq, fp64_tol):
+    """Mixed and incremental builds (two tiers, or three with a double-float
+    band up to 1e-2) converge to the all-FP64 energy: the last iterations
+    are all-FP64 builds."""
     mol, bas = _mixed_case()
     nocc = mol.n_electrons(mol.closed_shell_charge()) // 2
     b = cq.Basis(mol, bas)
     _, _, st64 = b.scf(nocc)
-    _, _, stm = b.scf(nocc, prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, incremental=True)
+    _, _, stm = b.scf(nocc, prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4, incremental=True, fp64_tol=fp64_tol)
     assert stm["converged"]
     assert stm["quartets_fp32"] > 0
+    assert (stm["quartets_df"] > 0) == (fp64_tol > 0)
     assert abs(stm["energy"] - st64["energy"]) < 1e-10
 
 
@@ -99,6 +104,31 @@ def test_rt_matches_oracle_step_by_step(cq, dr):
         assert abs(g["energy"] - o[2]) < 1e-10
     assert gobs[0]["em2"] and gobs[5]["em2"] and not gobs[1]["em2"]
     assert abs(gobs[0]["energy"] - r.energy) < 1e-10
+
+
+def test_rt_double_float_matches_oracle(cq, dr):
+    """RT steps whose Fock builds run every quartet in double-float (mixed
+    precision with mixed_tol 0 and no FP64 tier) follow the FP64 oracle at
+    the FP64 tolerances."""
+    import torch
+    mol, bas = synth.workload_triatomic()
+    b = cq.Basis(mol, bas)
+    D, _, _ = b.scf(5)
+    Pc = D.to(torch.complex128).clone()
+    Pp = Pc.clone()
+    s = dr.System(mol, bas)
+    field = dict(field=(0.0, 0.0, 1e-3), t_on=0.0, t_off=0.05)
+    rt = dr.RT(s, D.cpu().numpy(), 0.05, dr.Field((0.0, 0.0, 1e-3), 0.0, 0.05), restart=5)
+    kw = dict(prec=cq.CQ_PREC_MIXED, mixed_tol=0.0, fp64_tol=1e300)
+    gobs, oobs = [], []
+    for k in range(12):
+        gobs.append(b.rt_step(k, Pp, Pc, dt=0.05, restart_every=5, **field, **kw))
+        oobs.append(rt.step())
+    for k in range(11):
+        g, o = gobs[k + 1], oobs[k]
+        assert np.abs(np.array(g["dipole"]) - o[0]).max() < 1e-9, k
+        assert abs(g["trPS"] - o[1]) < 1e-10
+        assert abs(g["energy"] - o[2]) < 1e-9
 
 
 def test_rt_zero_field_stationary(cq):
