@@ -16,6 +16,10 @@ namespace cq {
 using ::fma;
 using ::fmaf;
 
+// The arithmetic compiles for the host too (a host program checks it
+// against exact rational arithmetic); the shuffles and 1/sqrt are device
+// code.
+
 struct df {
     float hi, lo;
     df() = default;
@@ -27,29 +31,29 @@ struct df {
     __host__ __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
-__device__ __forceinline__ df df_two_sum(float a, float b)
+__host__ __device__ __forceinline__ df df_two_sum(float a, float b)
 {
     const float s = a + b;
     const float bb = s - a;
     return df(s, (a - (s - bb)) + (b - bb));
 }
 
-__device__ __forceinline__ df df_fast_two_sum(float a, float b)   // |a| >= |b| or a == 0
+__host__ __device__ __forceinline__ df df_fast_two_sum(float a, float b)   // |a| >= |b| or a == 0
 {
     const float s = a + b;
     return df(s, b - (s - a));
 }
 
-__device__ __forceinline__ df operator+(df a, df b)
+__host__ __device__ __forceinline__ df operator+(df a, df b)
 {
     const df s = df_two_sum(a.hi, b.hi);
     return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
 
-__device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
-__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__host__ __device__ __forceinline__ df operator-(df a) { return df(-a.hi, -a.lo); }
+__host__ __device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
 
-__device__ __forceinline__ df operator*(df a, df b)
+__host__ __device__ __forceinline__ df operator*(df a, df b)
 {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
@@ -58,7 +62,7 @@ __device__ __forceinline__ df operator*(df a, df b)
 }
 
 // a * b + c with one renormalisation
-__device__ __forceinline__ df fma(df a, df b, df c)
+__host__ __device__ __forceinline__ df fma(df a, df b, df c)
 {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
@@ -67,9 +71,9 @@ __device__ __forceinline__ df fma(df a, df b, df c)
     return df_fast_two_sum(s.hi, s.lo + (e + c.lo));
 }
 
-__device__ __forceinline__ df& operator+=(df& a, df b) { a = a + b; return a; }
-__device__ __forceinline__ df& operator*=(df& a, df b) { a = a * b; return a; }
-__device__ __forceinline__ bool operator<(df a, float b) { return a.hi < b || (a.hi == b && a.lo < 0.f); }
+__host__ __device__ __forceinline__ df& operator+=(df& a, df b) { a = a + b; return a; }
+__host__ __device__ __forceinline__ df& operator*=(df& a, df b) { a = a * b; return a; }
+__host__ __device__ __forceinline__ bool operator<(df a, float b) { return a.hi < b || (a.hi == b && a.lo < 0.f); }
 
 // warp shuffles of a double-float (both words)
 __device__ __forceinline__ df shfl_down_r(df v, int o)
@@ -96,7 +100,7 @@ __device__ __forceinline__ df rsqrt_r(df x)
 }
 
 // 1/x: FP32 estimate and one Newton step, r <- r + r (1 - x r)
-__device__ __forceinline__ df recip(df x)
+__host__ __device__ __forceinline__ df recip(df x)
 {
     const float r0 = 1.0f / x.hi;
     const df r(r0, 0.f);
@@ -105,7 +109,7 @@ __device__ __forceinline__ df recip(df x)
 }
 
 // sqrt(x), x > 0: s <- s + (x - s^2) / (2 s)
-__device__ __forceinline__ df sqrt_df(df x)
+__host__ __device__ __forceinline__ df sqrt_df(df x)
 {
     const float s0 = sqrtf(x.hi);
     const df s(s0, 0.f);
