@@ -11,8 +11,9 @@ density bound is below mixed_tol, double-float -- FP32 pairs -- up to
 fp64_tol, FP64 above; everything accumulated exactly), with the
 energy error against the all-FP64 GPU build checked in the same run
 (|dE| <= 1e-6 Eh).  The all-FP64 rate is reported beside it.  The same run
-then times the 100-atom, 1930-function single build (split FP32/FP64,
-Schwarz 1e-12) under the key "large100" (--large-steps, 0 to skip).
+then times the 100-atom, 1930-function single build (the same three tiers,
+mixed_tol 3e-3, Schwarz 1e-12) under the key "large100" (--large-steps, 0
+to skip).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec mixed|fp64]
   python bench.py --impl reference ...   # the CPU oracle on the same workload
@@ -38,14 +39,15 @@ import synth  # noqa: E402
 METRIC = "J+K Fock builds/s & ERI quartets/s; mixed vs FP64 GPU at |dE|<=1e-6 Eh"
 WORKLOAD = "rt16: 16-atom O6H10 cluster, 210 Cartesian s,p,d functions, complex-Hermitian P (29 occ)"
 # precision split of the headline build: the mixed_tol sweep of this
-# workload (--workload tolsweep) gives |dE| 2.3e-7 Eh at 5e-3 (target 1e-6,
-# a 4x margin; 1e-2 leaves 8.3e-7, too close), checked again in every run
+# workload (--workload tolsweep) gives |dE| 0.3-2.3e-7 Eh at 5e-3 (target
+# 1e-6; 1e-2 leaves 2.5e-7 to 8.3e-7 and element errors of 2.5e-6, too
+# close), checked again in every run
 MIXED_TOL = 5e-3
 # double-float tier of the mixed builds: quartets with mixed_tol <= bound <
 # FP64_TOL in pairs of FP32 values (~48 bits, on the FP32 pipes), bound >=
 # FP64_TOL in FP64.  The sweep at mixed_tol 5e-3 (--workload tolsweep):
-# two tiers 287-350 ms, FP64_TOL 0.1 117-135 ms, 1.0 109-127 ms, |dE| the
-# same to 1e-14 Eh; FP64 keeps the quartets bounded above 1 Eh
+# two tiers 173 ms, FP64_TOL 0.1 107 ms, 1.0 98 ms, |dE| the same to 1e-14
+# Eh; FP64 keeps the quartets bounded above 1 Eh
 FP64_TOL = 1.0
 # the RT-TDHF comparison keeps a tighter split: its mixed run never returns
 # to all-FP64 builds, and the dipole error grows with the split
@@ -60,8 +62,8 @@ def workload():
     return mol, bas, P
 
 
-# the large single J/K build: 100-atom cluster, split FP32/FP64 precision
-# (the tighter 3e-3 split: its energy error against an all-FP64 build is not
+# the large single J/K build: 100-atom cluster, three precision tiers (the
+# tighter 3e-3 split: its energy error against an all-FP64 build is not
 # measured in the benchmark run)
 LARGE_WORKLOAD = ("large100: 100-atom cluster (H with p 0.25, else C/N/O), 1930 Cartesian s,p,d functions, "
                   "real P of 200 random orthonormal orbitals, Schwarz 1e-12")
