@@ -432,14 +432,6 @@ int classify_and_launch(const cq_basis* b, JKArgs& a, const cq_fock_opts& o, boo
     return CQ_OK;
 }
 
-static int class_L(int qc)
-{
-    int X = 0;
-    while ((X + 1) * (X + 2) / 2 <= qc) ++X;
-    const int Y = qc - X * (X + 1) / 2;
-    return PC_L[X][0] + PC_L[X][1] + PC_L[Y][0] + PC_L[Y][1];
-}
-
 // Cooperative kernel on the screened list, split per the basis's list_split
 // and list_chunk.  The FP64 pipe of an SM runs at 1/62 of its FP32 rate, so
 // the deep quartets of short FP64 lists pay to be spread over many warps
