@@ -662,6 +662,56 @@ def run_cluster30(args):
     return 0
 
 
+def run_transition(args):
+    """J+K of a ph-RPA transition density on the 16-atom workload: D = C_o X
+    C_v^T (random orthonormal occupied and virtual orbitals, random X; no
+    symmetry), builds/s in FP64 and with the headline's three tiers, and the
+    mixed build's errors against the FP64 one."""
+    torch, cq = _driver_setup()
+    if cq is None:
+        return 0
+    mol, bas = synth.workload_rt16()
+    b = cq.Basis(mol, bas)
+    n = b.nbf
+    C = synth.orbitals(n, n, 7)
+    X = synth.rng(8).standard_normal((NOCC, n - NOCC)) / np.sqrt(NOCC * (n - NOCC))
+    D = torch.as_tensor(C[:, :NOCC] @ X @ C[:, NOCC:].T, device="cuda")
+    kind = cq.CQ_DENS_REAL_GENERAL
+    b.autotune(D, prec=cq.CQ_PREC_FP64, cache=False, kind=kind)
+    b.autotune(D, prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL, cache=False, kind=kind)
+    flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    modes = {"fp64": dict(prec=cq.CQ_PREC_FP64),
+             "mixed": dict(prec=cq.CQ_PREC_MIXED, mixed_tol=MIXED_TOL, fp64_tol=FP64_TOL)}
+    out, ms = {}, {}
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        for name, kw in modes.items():
+            for _ in range(args.warmup):
+                b.fock_build(D, kind=kind, **kw)
+            tms = []
+            for _ in range(max(1, args.steps)):
+                flush_l2(flush)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out[name] = b.fock_build(D, kind=kind, **kw)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tms.append(e0.elapsed_time(e1))
+            ms[name] = statistics.median(tms)
+    (J64, K64), (Jm, Km) = out["fp64"], out["mixed"]
+    dJ = float((Jm - J64).abs().max().item())
+    dK = float((Km - K64).abs().max().item())
+    b.close()
+    _line("J+K builds/s of a non-Hermitian (transition) density, mixed vs FP64", 1e3 / ms["mixed"], "builds/s",
+          True, args, ms["mixed"],
+          {"workload": WORKLOAD.replace("complex-Hermitian P (29 occ)",
+                                        "real transition density C_o X C_v^T (29 occ, 181 virt)"),
+           "mixed_tol": MIXED_TOL, "fp64_tol": FP64_TOL, "l2": "flushed (256 MiB write) between timed builds"},
+          {"fp64_builds_per_s": 1e3 / ms["fp64"], "max_dJ_mixed_vs_fp64": dJ, "max_dK_mixed_vs_fp64": dK,
+           "max_abs_K_asymmetry": float((K64 - K64.T).abs().max().item())}, clk, None)
+    return 0
+
+
 def run_scf(args):
     """RHF direct SCF on the 16-atom workload: time to the converged energy,
     all-FP64 against mixed precision with incremental builds."""
@@ -840,9 +890,11 @@ def main():
                     help="keep the default kernel variant per class (profiling runs)")
     ap.add_argument("--variant", action="append", default=[], metavar="QC:PREC:V",
                     help="set the kernel variant of one class and precision (0 FP64, 1 FP32, 2 double-float; after autotuning)")
-    ap.add_argument("--workload", default="jk", choices=["jk", "scf", "rt", "batch", "tolsweep", "cluster30"],
+    ap.add_argument("--workload", default="jk",
+                    choices=["jk", "scf", "rt", "batch", "tolsweep", "cluster30", "transition"],
                     help="jk: the headline J+K build rate; scf / rt / batch: the drivers "
-                         "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess)")
+                         "(RHF time to converged energy, RT-TDHF steps, batched SCF with the learned guess); "
+                         "transition: J+K of a non-Hermitian transition density")
     ap.add_argument("--tuning-cache", action="store_true",
                     help="reuse (or store) the autotuned variant table instead of re-tuning")
     ap.add_argument("--large-steps", type=int, default=1,
@@ -869,6 +921,8 @@ def main():
         return run_tol_sweep(args)
     if args.workload == "cluster30":
         return run_cluster30(args)
+    if args.workload == "transition":
+        return run_transition(args)
     return run_gpu(args)
 
 

@@ -55,7 +55,12 @@ typedef enum {
 typedef enum {
     CQ_DENS_REAL_SYM = 0,      /* P real symmetric (one spin block, RHF)     */
     CQ_DENS_COMPLEX_HERM = 1,  /* P complex Hermitian (RT-TDHF, one block)   */
-    CQ_DENS_PAULI4 = 2         /* P^0..P^3 complex Hermitian (GHF, 2C)       */
+    CQ_DENS_PAULI4 = 2,        /* P^0..P^3 complex Hermitian (GHF, 2C)       */
+    CQ_DENS_REAL_GENERAL = 3   /* P real, any symmetry: the transition
+                                  densities of the direct ph-RPA products,
+                                  contracted as in Eq. 2c_fock with a
+                                  non-Hermitian density (Sec. "Residue
+                                  Methods")                                  */
 } cq_dens_kind;
 
 typedef enum { CQ_PREC_FP64 = 0, CQ_PREC_MIXED = 1 } cq_prec;
@@ -149,11 +154,16 @@ typedef struct {
  *                  antisymmetric Im P vanishes); K nbf^2 c128 (Hermitian).
  *   PAULI4:        P 4*nbf^2 c128 (P^0..P^3, each Hermitian); J nbf^2 f64 =
  *                  J[P^0]; K 4*nbf^2 c128 = K[P^0..P^3].
+ *   REAL_GENERAL:  P nbf^2 f64 (any symmetry); J nbf^2 f64 (J of the
+ *                  symmetric part; that of the antisymmetric part vanishes);
+ *                  K nbf^2 f64 = K[P] = K[S] + K[A] (S, A the symmetric and
+ *                  antisymmetric parts, built as the real and imaginary
+ *                  parts of the Hermitian S + iA).
  * J or K may be NULL when opts->want_J / want_K is 0.  opts NULL = defaults
  * (schwarz_tol 1e-14, FP64, J and K).  stats may be NULL; when given, the
  * call synchronises `stream` to fill it.  Hermiticity of P is assumed, not
- * checked: only the symmetric part of Re P and the antisymmetric part of
- * Im P contribute. */
+ * checked (except for REAL_GENERAL): only the symmetric part of Re P and
+ * the antisymmetric part of Im P contribute. */
 int cq_fock_build(cq_basis* b, int kind, const void* P, double* J, void* K,
                   const cq_fock_opts* opts, cq_fock_stats* stats, void* stream);
 

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libcq.so")
 _lib = None
 
-CQ_DENS_REAL_SYM, CQ_DENS_COMPLEX_HERM, CQ_DENS_PAULI4 = 0, 1, 2
+CQ_DENS_REAL_SYM, CQ_DENS_COMPLEX_HERM, CQ_DENS_PAULI4, CQ_DENS_REAL_GENERAL = 0, 1, 2, 3
 CQ_PREC_FP64, CQ_PREC_MIXED = 0, 1
 
 
@@ -304,7 +304,9 @@ class Basis:
                    want_J=True, want_K=True, J=None, K=None, stats=False, stream=None, fp64_tol=0.0):
         """J, K of a density given as a torch CUDA tensor:
         float64 (n, n) real symmetric; complex128 (n, n) Hermitian;
-        complex128 (4, n, n) Pauli components P^0..P^3.  In mixed precision,
+        complex128 (4, n, n) Pauli components P^0..P^3; with
+        kind=CQ_DENS_REAL_GENERAL, float64 (n, n) of any symmetry (real J and
+        K, e.g. of a transition density).  In mixed precision,
         fp64_tol > mixed_tol adds the double-float tier for bounds in
         [mixed_tol, fp64_tol)."""
         import torch
@@ -321,7 +323,7 @@ class Basis:
         if want_J and J is None:
             J = torch.empty(shape, dtype=torch.float64, device=P.device)
         if want_K and K is None:
-            if kind == CQ_DENS_REAL_SYM:
+            if kind in (CQ_DENS_REAL_SYM, CQ_DENS_REAL_GENERAL):
                 K = torch.empty(shape, dtype=torch.float64, device=P.device)
             elif kind == CQ_DENS_COMPLEX_HERM:
                 K = torch.empty(shape, dtype=torch.complex128, device=P.device)
@@ -447,7 +449,7 @@ class Basis:
         return v.value
 
     def autotune(self, P, prec=CQ_PREC_MIXED, mixed_tol=1e-3, schwarz_tol=1e-14, fp64_tol=0.0, cache=True,
-                 stream=None):
+                 stream=None, kind=None):
         """Pick the fastest kernel variant per class and precision (see
         cq_autotune) for builds with these options.  With cache=True the
         choice is stored per GPU model and split in _build/tuning.json and
@@ -466,8 +468,9 @@ class Basis:
                     for p, v in enumerate(row):
                         self.set_variant(qc, p, v)
                 return tab
-        kind = (CQ_DENS_REAL_SYM if P.dtype == torch.float64 else
-                CQ_DENS_PAULI4 if P.dim() == 3 else CQ_DENS_COMPLEX_HERM)
+        if kind is None:
+            kind = (CQ_DENS_REAL_SYM if P.dtype == torch.float64 else
+                    CQ_DENS_PAULI4 if P.dim() == 3 else CQ_DENS_COMPLEX_HERM)
         o = FockOpts(schwarz_tol, mixed_tol, prec, 1, 1, fp64_tol)
         tab = (ctypes.c_int * 63)()
         ms = (ctypes.c_double * 63)()

@@ -46,6 +46,11 @@ __global__ void density_prep_kernel(int kind, int nmol, int ld, const int* __res
     } else if (kind == CQ_DENS_COMPLEX_HERM) {
         Dp[i] = f * P[2 * i];
         Dp[ms + i] = f * P[2 * i + 1];
+    } else if (kind == CQ_DENS_REAL_GENERAL) {
+        // symmetric and antisymmetric parts, handled as Re and Im of S + iA
+        const size_t t = (size_t)m * slot + (size_t)c * ld + r;
+        Dp[i] = 0.5 * f * (P[i] + P[t]);
+        Dp[ms + i] = 0.5 * f * (P[i] - P[t]);
     } else {
         for (int I = 0; I < 4; ++I) {
             Dp[(2 * I) * ms + i] = f * P[2 * (I * ms + i)];
@@ -106,6 +111,8 @@ __global__ void finalize_kernel(int kind, int nmol, int ld, const int* __restric
     } else if (kind == CQ_DENS_COMPLEX_HERM) {
         K[2 * i] = f * fx_pair(Kp, i, t, false);
         K[2 * i + 1] = f * fx_pair(Kp + 2 * ms, i, t, true);
+    } else if (kind == CQ_DENS_REAL_GENERAL) {
+        K[i] = f * (fx_pair(Kp, i, t, false) + fx_pair(Kp + 2 * ms, i, t, true));   // K[S] + K[A]
     } else {
         for (int I = 0; I < 4; ++I) {
             const acc_t* Kr = Kp + 2 * (2 * I) * ms;
@@ -127,7 +134,7 @@ __global__ void counter_total_kernel(unsigned long long* c)
     }
 }
 
-static int nk_of(int kind) { return kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8; }
+static int nk_of(int kind) { return dens_nk(kind); }
 
 int ensure_scratch(cq_basis* b, int nk)
 {
@@ -571,7 +578,7 @@ int cq::fock_build_modes(cq_basis* b, int kind, const void* P, double* J, void* 
                      cq_fock_stats* stats, cudaStream_t s, const int* mol_mode, unsigned long long* acc)
 {
     if (!b || !P) { set_error("cq_fock_build: NULL basis or density"); return CQ_ERR_INVALID_ARG; }
-    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_PAULI4) {
+    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_REAL_GENERAL) {
         set_error("cq_fock_build: unknown density kind");
         return CQ_ERR_INVALID_ARG;
     }

@@ -16,6 +16,11 @@ struct JKArgs;
 constexpr int NPC = 6;
 constexpr int NQC = 21;   // (bra class X) >= (ket class Y)
 inline int pc_of(int la, int lb) { return la * (la + 1) / 2 + lb; }
+// real density matrices a build contracts for each density kind
+inline int dens_nk(int kind)
+{
+    return kind == CQ_DENS_REAL_SYM ? 1 : (kind == CQ_DENS_COMPLEX_HERM || kind == CQ_DENS_REAL_GENERAL) ? 2 : 8;
+}
 extern const int PC_L[NPC][2];
 
 using LaunchJK = void (*)(const JKArgs&, int fp32, cudaStream_t);

@@ -73,7 +73,7 @@ using namespace cq;
 // largest molecule (noalloc_bytes below, which the call itself checks).
 extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
 {
-    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const int nk = dens_nk(kind);
     const size_t nn = (size_t)nbf * nbf;
     return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
            round256(2 * nn * sizeof(acc_t)) + round256((size_t)nshell * nshell * sizeof(float)) +
@@ -82,7 +82,7 @@ extern "C" size_t cq_fock_noalloc_scratch_bytes(int kind, int nbf, int nshell)
 
 static size_t noalloc_bytes(const cq_basis* b, int kind)
 {
-    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const int nk = dens_nk(kind);
     const size_t nn = b->mstride;
     return round256(nn * nk * sizeof(double)) + round256(2 * nn * nk * sizeof(acc_t)) +
            round256(2 * nn * sizeof(acc_t)) + round256((size_t)b->nmol * b->lds * b->lds * sizeof(float)) +
@@ -93,7 +93,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
                                      const cq_fock_opts* opts, void* stream)
 {
     if (!b || !P) { set_error("cq_fock_build_noalloc: NULL basis or density"); return CQ_ERR_INVALID_ARG; }
-    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_PAULI4) {
+    if (kind < CQ_DENS_REAL_SYM || kind > CQ_DENS_REAL_GENERAL) {
         set_error("cq_fock_build_noalloc: unknown density kind");
         return CQ_ERR_INVALID_ARG;
     }
@@ -117,7 +117,7 @@ extern "C" int cq_fock_build_noalloc(cq_basis* b, int kind, const void* P, doubl
     void* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
-    const int nk = kind == CQ_DENS_REAL_SYM ? 1 : kind == CQ_DENS_COMPLEX_HERM ? 2 : 8;
+    const int nk = dens_nk(kind);
     const int n = b->ld;
     const size_t nn = b->mstride;
     unsigned char* p = (unsigned char*)base;

@@ -309,3 +309,27 @@ def test_double_float_tier(cq, orc, name):
     assert st3["quartets_fp32"] == st2["quartets_fp32"]
     assert np.abs(J3.cpu().numpy() - Jo).max() < 1e-6
     assert np.abs(K3.cpu().numpy() - Ko).max() < 1e-6
+
+
+@pytest.mark.parametrize("name", ["OCNH3", "O1H2_deep"])
+def test_non_hermitian_density(cq, orc, name):
+    """J and K of a real density of no symmetry (the transition densities of
+    the direct ph-RPA products): FP64 against the oracle's contraction of
+    the full definition at the FP64 tolerance, three tiers at the mixed one;
+    J is that of the symmetric part alone."""
+    mol, bas = CASES[name]()
+    b = cq.Basis(mol, bas)
+    g = np.random.default_rng(21)
+    D = 0.1 * g.standard_normal((b.nbf, b.nbf))
+    Jo, Ko = orc.jk(orc.OBasis(mol, bas), D)
+    J, K = b.fock_build(_gpu(D), kind=cq.CQ_DENS_REAL_GENERAL)
+    assert np.abs(J.cpu().numpy() - Jo).max() < TOL
+    assert np.abs(K.cpu().numpy() - Ko).max() < TOL
+    assert np.abs(Ko - Ko.T).max() > 1e-3                     # K of a non-symmetric D is not symmetric
+    J3, K3, st = b.fock_build(_gpu(D), kind=cq.CQ_DENS_REAL_GENERAL, prec=cq.CQ_PREC_MIXED, mixed_tol=1e-4,
+                              fp64_tol=1e-2, stats=True)
+    assert st["quartets_fp32"] > 0 and st["quartets_df"] > 0
+    assert np.abs(J3.cpu().numpy() - Jo).max() < 1e-6
+    assert np.abs(K3.cpu().numpy() - Ko).max() < 1e-6
+    Js, _ = b.fock_build(_gpu(0.5 * (D + D.T)))
+    assert np.abs(Js.cpu().numpy() - J.cpu().numpy()).max() < 1e-12
